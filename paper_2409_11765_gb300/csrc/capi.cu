@@ -1,0 +1,759 @@
+// capi.cu -- the engine behind include/cmaes.h: device memory layout, the
+// per-generation launch schedule, ask/tell, checkpoints and error handling.
+//
+// One handle holds `count` searches in one device arena. A generation is a
+// fixed sequence of batched launches (sample, objective, rank + update,
+// covariance, eigendecomposition when due, stop + restart), each covering all
+// searches at once through prefix-summed tile lists; searches that are done or
+// whose eigendecomposition is not due leave their tiles at once. All control
+// decisions (restarts, lambda doubling, the lazy eigendecomposition cadence)
+// are taken on the device, so the host only enqueues work.
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "../../include/cmaes.h"
+#include "engine.h"
+
+using namespace cmaes_gb300;
+
+namespace {
+
+struct PendingEvents {
+  int first;  // index of the first of kNumPhases + 1 events in the pool
+};
+
+}  // namespace
+
+struct cmaes_s {
+  int count = 0;
+  cmaes_options opt{};
+  DevOptions dopt{};
+  std::vector<Search> hs;  // host copies (constant fields authoritative)
+  Search* dS = nullptr;
+  char* arena = nullptr;
+  size_t arena_bytes = 0;
+  int* d_off = nullptr;  // TK_COUNT x (count + 1)
+  std::vector<int> h_off;
+  cudaStream_t stream = nullptr;
+  cmaes_status err = CMAES_OK;
+  std::string msg;
+  std::vector<int> ask_pending;
+  int max_n = 0, max_n_smem_jacobi = 0, max_n_global_jacobi = 0;
+  bool any_rotated = false;
+  long long launches = 0;
+  // profiling
+  bool profiling = false;
+  std::vector<cudaEvent_t> pool;
+  std::vector<PendingEvents> pending;
+  double phase_ms[kNumPhases] = {0};
+  long long phase_launch[kNumPhases] = {0};
+
+  TileMap tiles(int kind, int s0, int s1) const {
+    TileMap tm;
+    tm.off = d_off + static_cast<size_t>(kind) * (count + 1);
+    tm.s0 = s0;
+    tm.s1 = s1;
+    const int* o = h_off.data() + static_cast<size_t>(kind) * (count + 1);
+    tm.total = o[s1] - o[s0];
+    return tm;
+  }
+};
+
+static std::string g_create_error;
+
+static cmaes_status set_error(cmaes_t h, cmaes_status st, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  if (h) {
+    h->msg = buf;
+    if (st == CMAES_ECUDA) h->err = CMAES_ECUDA;
+  } else {
+    g_create_error = buf;
+  }
+  return st;
+}
+
+#define CUDA_TRY(h, call)                                                                      \
+  do {                                                                                         \
+    cudaError_t e_ = (call);                                                                   \
+    if (e_ != cudaSuccess)                                                                     \
+      return set_error((h), CMAES_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));      \
+  } while (0)
+
+#define CHECK_HANDLE(h)                           \
+  do {                                            \
+    if (!(h)) return CMAES_EINVAL;                \
+    if ((h)->err != CMAES_OK) return (h)->err;    \
+  } while (0)
+
+#define CHECK_SEARCH(h, s)                                                            \
+  do {                                                                                \
+    if ((s) < 0 || (s) >= (h)->count)                                                 \
+      return set_error((h), CMAES_EINVAL, "search index %d out of range [0, %d)", (s), \
+                       (h)->count);                                                   \
+  } while (0)
+
+static size_t align256(size_t b) { return (b + 255) & ~static_cast<size_t>(255); }
+
+static int default_lambda(int n) { return 4 + static_cast<int>(std::floor(3.0 * std::log(static_cast<double>(n)))); }
+
+static cmaes_status launch_check(cmaes_t h, const char* what) {
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return set_error(h, CMAES_ECUDA, "launch of %s failed: %s", what, cudaGetErrorString(e));
+  return CMAES_OK;
+}
+
+static cmaes_status read_search(cmaes_t h, int s, Search* out) {
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(out, h->dS + s, sizeof(Search), cudaMemcpyDeviceToHost));
+  return CMAES_OK;
+}
+
+static cmaes_status write_search(cmaes_t h, int s, const Search* in) {
+  CUDA_TRY(h, cudaMemcpy(h->dS + s, in, sizeof(Search), cudaMemcpyHostToDevice));
+  return CMAES_OK;
+}
+
+// ------------------------------ phase schedule ------------------------------
+// Counts the launches each launcher actually issues (grids of zero are not
+// launched).
+static inline void count_launch(cmaes_t h, int phase, int total) {
+  if (total > 0) {
+    h->launches += 1;
+    h->phase_launch[phase] += 1;
+  }
+}
+
+static void enqueue_sample(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap a = h->tiles(TK_SAMPLE_Z, s0, s1), b = h->tiles(TK_PANEL, s0, s1);
+  launch_sample_z(h->dS, a, h->dopt, st);
+  count_launch(h, kPhaseSample, a.total);
+  launch_gemm_sample(h->dS, b, st);
+  count_launch(h, kPhaseSample, b.total);
+}
+
+static void enqueue_objective(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap a = h->tiles(TK_PANEL, s0, s1), b = h->tiles(TK_COLRED, s0, s1);
+  if (h->any_rotated) {
+    launch_gemm_objective(h->dS, a, st);
+    count_launch(h, kPhaseObjective, a.total);
+  }
+  launch_colreduce_f(h->dS, b, st);
+  count_launch(h, kPhaseObjective, b.total);
+}
+
+static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap r = h->tiles(TK_RANK, s0, s1), rc = h->tiles(TK_RECOMB, s0, s1);
+  TileMap rows = h->tiles(TK_ROWS, s0, s1), gv = h->tiles(TK_GEMV, s0, s1);
+  launch_rank(h->dS, r, st);
+  count_launch(h, kPhaseUpdate, r.total);
+  launch_recomb_partial(h->dS, rc, st);
+  count_launch(h, kPhaseUpdate, rc.total);
+  launch_recomb_final(h->dS, rows, st);
+  count_launch(h, kPhaseUpdate, rows.total);
+  launch_psigma_partial(h->dS, gv, st);
+  count_launch(h, kPhaseUpdate, gv.total);
+  launch_psigma_final(h->dS, rows, st);
+  count_launch(h, kPhaseUpdate, rows.total);
+  launch_finalize(h->dS, s0, s1, h->dopt, st);
+  count_launch(h, kPhaseUpdate, s1 - s0);
+}
+
+static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap t = h->tiles(TK_SYM, s0, s1);
+  launch_cov(h->dS, t, st);
+  count_launch(h, kPhaseCov, t.total);
+}
+
+static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap sq = h->tiles(TK_SQUARE, s0, s1);
+  launch_eig_gemm_CB(h->dS, sq, st);
+  count_launch(h, kPhaseEig, sq.total);
+  launch_eig_gemm_BtT(h->dS, sq, st);
+  count_launch(h, kPhaseEig, sq.total);
+  if (h->max_n_smem_jacobi > 0) {
+    launch_jacobi_variant(h->dS, s0, s1, true, h->max_n_smem_jacobi, st);
+    count_launch(h, kPhaseEig, s1 - s0);
+  }
+  if (h->max_n_global_jacobi > 0) {
+    launch_jacobi_variant(h->dS, s0, s1, false, h->max_n_global_jacobi, st);
+    count_launch(h, kPhaseEig, s1 - s0);
+  }
+  launch_set_bd(h->dS, sq, st);
+  count_launch(h, kPhaseEig, sq.total);
+}
+
+static void enqueue_stop(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  launch_stop(h->dS, s0, s1, h->dopt, st);
+  count_launch(h, kPhaseStop, s1 - s0);
+}
+
+static cmaes_status record_event(cmaes_t h, int idx, cudaStream_t st) {
+  CUDA_TRY(h, cudaEventRecord(h->pool[idx], st));
+  return CMAES_OK;
+}
+
+static cmaes_status drain_events(cmaes_t h) {
+  if (h->pending.empty()) return CMAES_OK;
+  CUDA_TRY(h, cudaEventSynchronize(h->pool[h->pending.back().first + kNumPhases]));
+  for (const PendingEvents& p : h->pending) {
+    for (int k = 0; k < kNumPhases; ++k) {
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, h->pool[p.first + k], h->pool[p.first + k + 1]));
+      h->phase_ms[k] += ms;
+    }
+  }
+  h->pending.clear();
+  return CMAES_OK;
+}
+
+static cmaes_status enqueue_generation(cmaes_t h, int s0, int s1, cudaStream_t st, bool with_objective) {
+  const bool prof = h->profiling;
+  int base = 0;
+  if (prof) {
+    const int need = kNumPhases + 1;
+    if (static_cast<int>(h->pool.size()) < static_cast<int>(h->pending.size() + 1) * need) {
+      if (h->pool.size() >= 4096) {
+        cmaes_status r = drain_events(h);
+        if (r != CMAES_OK) return r;
+      }
+      while (static_cast<int>(h->pool.size()) < static_cast<int>(h->pending.size() + 1) * need) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreate(&e));
+        h->pool.push_back(e);
+      }
+    }
+    base = static_cast<int>(h->pending.size()) * need;
+    h->pending.push_back({base});
+  }
+  auto mark = [&](int k) -> cmaes_status {
+    return prof ? record_event(h, base + k, st) : CMAES_OK;
+  };
+  cmaes_status r;
+  if ((r = mark(0)) != CMAES_OK) return r;
+  if (with_objective) enqueue_sample(h, s0, s1, st);
+  if ((r = mark(1)) != CMAES_OK) return r;
+  if (with_objective) enqueue_objective(h, s0, s1, st);
+  if ((r = mark(2)) != CMAES_OK) return r;
+  enqueue_update(h, s0, s1, st);
+  if ((r = mark(3)) != CMAES_OK) return r;
+  enqueue_cov(h, s0, s1, st);
+  if ((r = mark(4)) != CMAES_OK) return r;
+  enqueue_eig(h, s0, s1, st);
+  if ((r = mark(5)) != CMAES_OK) return r;
+  enqueue_stop(h, s0, s1, st);
+  if ((r = mark(6)) != CMAES_OK) return r;
+  return launch_check(h, "generation");
+}
+
+// ---------------------------------- ABI -------------------------------------
+extern "C" {
+
+void cmaes_default_options(cmaes_options* o) {
+  if (!o) return;
+  std::memset(o, 0, sizeof(*o));
+  o->precision = CMAES_FP64;
+  o->max_restarts = 0;
+  o->ipop_double = 1;
+  o->eig_every = 0;
+  o->max_iter = 0;
+  o->stop_mask = CMAES_STOP_ALL;
+  o->f_target = -INFINITY;
+  o->box_lo = -4.0;
+  o->box_hi = 4.0;
+  o->tol_hist_fun = 1e-12;
+  o->tol_x_factor = 1e-12;
+  o->cond_max = 1e14;
+}
+
+const char* cmaes_strerror(cmaes_status st) {
+  switch (st) {
+    case CMAES_OK: return "ok";
+    case CMAES_EINVAL: return "invalid argument";
+    case CMAES_ENOMEM: return "out of memory";
+    case CMAES_ECUDA: return "CUDA error";
+    case CMAES_ESTATE: return "call out of order";
+    case CMAES_ETIMEOUT: return "device wait timed out";
+    case CMAES_ENUMERIC: return "non-finite state";
+    case CMAES_EUNSUPPORTED: return "unsupported";
+  }
+  return "unknown status";
+}
+
+const char* cmaes_last_error(cmaes_t h) { return h ? h->msg.c_str() : g_create_error.c_str(); }
+
+void cmaes_destroy(cmaes_t h) {
+  if (!h) return;
+  if (h->stream) cudaStreamSynchronize(h->stream);
+  for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
+  if (h->arena) cudaFree(h->arena);
+  if (h->dS) cudaFree(h->dS);
+  if (h->d_off) cudaFree(h->d_off);
+  if (h->stream) cudaStreamDestroy(h->stream);
+  delete h;
+}
+
+cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr, const double* const* x0,
+                                const double* sigma0, uint64_t seed, const cmaes_options* opt_in,
+                                cmaes_t* out) {
+  if (!out) return set_error(nullptr, CMAES_EINVAL, "out is NULL");
+  *out = nullptr;
+  if (count < 1 || !n_arr || !x0 || !sigma0)
+    return set_error(nullptr, CMAES_EINVAL, "count must be >= 1 and n, x0, sigma0 non-NULL");
+  if (count > (1 << 24)) return set_error(nullptr, CMAES_EINVAL, "at most 2^24 searches");
+  cmaes_options opt;
+  if (opt_in) opt = *opt_in; else cmaes_default_options(&opt);
+  if (opt.precision != CMAES_FP64)
+    return set_error(nullptr, CMAES_EUNSUPPORTED, "precision %d not available in this build", opt.precision);
+  if (opt.max_restarts < 0 || opt.max_restarts > 255)
+    return set_error(nullptr, CMAES_EINVAL, "max_restarts must be in [0, 255]");
+  if (!(opt.box_lo < opt.box_hi)) return set_error(nullptr, CMAES_EINVAL, "box_lo must be < box_hi");
+
+  cmaes_t h = new cmaes_s();
+  h->count = count;
+  h->opt = opt;
+  DevOptions& d = h->dopt;
+  d.max_restarts = opt.max_restarts;
+  d.ipop_double = opt.ipop_double ? 1 : 0;
+  d.eig_every = opt.eig_every;
+  d.max_iter = opt.max_iter;
+  d.stop_mask = opt.stop_mask;
+  d.precision = opt.precision;
+  d.f_target = opt.f_target;
+  d.box_lo = opt.box_lo;
+  d.box_hi = opt.box_hi;
+  d.tol_hist_fun = opt.tol_hist_fun;
+  d.tol_x_factor = opt.tol_x_factor;
+  d.cond_max = opt.cond_max;
+  d.key0 = static_cast<uint32_t>(seed & 0xFFFFFFFFu);
+  d.key1 = static_cast<uint32_t>(seed >> 32);
+
+  // layout
+  h->hs.resize(count);
+  size_t total = 0;
+  std::vector<size_t> base(count);
+  const int jmax = jacobi_smem_max_n();
+  for (int s = 0; s < count; ++s) {
+    const int n = n_arr[s];
+    int lam = lam_arr ? lam_arr[s] : 0;
+    if (n < 1 || n > 65536) { delete h; return set_error(nullptr, CMAES_EINVAL, "search %d: n=%d out of range", s, n); }
+    if (lam == 0) lam = default_lambda(n);
+    if (lam < 2) { delete h; return set_error(nullptr, CMAES_EINVAL, "search %d: lambda=%d < 2", s, lam); }
+    if (!(sigma0[s] > 0.0) || !x0[s]) { delete h; return set_error(nullptr, CMAES_EINVAL, "search %d: bad sigma0 or x0", s); }
+    long long cap = opt.ipop_double ? (static_cast<long long>(lam) << opt.max_restarts) : lam;
+    if (cap > (1LL << 24)) { delete h; return set_error(nullptr, CMAES_EINVAL, "search %d: lambda capacity %lld too large", s, cap); }
+    Search& x = h->hs[s];
+    std::memset(&x, 0, sizeof(x));
+    x.n = n;
+    x.ldn = (n + 15) & ~15;
+    x.lam0 = lam;
+    x.lam_cap = static_cast<int>(cap);
+    x.mu_cap = x.lam_cap / 2;
+    x.hist_cap = 10 + static_cast<int>(std::ceil(30.0 * n / lam));
+    x.index = s;
+    x.obj = 0;
+    x.sigma0 = sigma0[s];
+    const size_t ldn = x.ldn, n_ = n, lc = x.lam_cap;
+    size_t b = 0;
+    b += 9 * align256(ldn * 8);                       // vectors
+    b += align256(static_cast<size_t>(x.mu_cap) * 8);  // w
+    b += align256(static_cast<size_t>(x.hist_cap) * 8);
+    b += align256(static_cast<size_t>(part_doubles(n, x.ldn, x.mu_cap)) * 8);
+    b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
+    b += 4 * align256(ldn * lc * 8);                   // Z Y X U
+    b += align256(lc * 8);                             // f
+    b += 2 * align256(lc * 4);                         // order rank
+    base[s] = total;
+    total += b;
+    if (n > h->max_n) h->max_n = n;
+    if (n <= jmax) { if (n > h->max_n_smem_jacobi) h->max_n_smem_jacobi = n; }
+    else if (n > h->max_n_global_jacobi) h->max_n_global_jacobi = n;
+  }
+  h->arena_bytes = total;
+  cudaError_t e = cudaMalloc(&h->arena, total);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    delete h;
+    return set_error(nullptr, CMAES_ENOMEM, "cudaMalloc of %zu bytes failed: %s", total, cudaGetErrorString(e));
+  }
+  auto fail = [&](cmaes_status st) {
+    g_create_error = h->msg;
+    cmaes_destroy(h);
+    return st;
+  };
+#define CREATE_TRY(call)                                                                         \
+  do {                                                                                           \
+    cudaError_t e_ = (call);                                                                     \
+    if (e_ != cudaSuccess) {                                                                     \
+      set_error(h, CMAES_ECUDA, "%s failed: %s", #call, cudaGetErrorString(e_));                \
+      return fail(CMAES_ECUDA);                                                                  \
+    }                                                                                            \
+  } while (0)
+  CREATE_TRY(cudaStreamCreateWithFlags(&h->stream, cudaStreamNonBlocking));
+  CREATE_TRY(cudaMemsetAsync(h->arena, 0, total, h->stream));
+  for (int s = 0; s < count; ++s) {
+    Search& x = h->hs[s];
+    char* p = h->arena + base[s];
+    const size_t ldn = x.ldn, n_ = x.n, lc = x.lam_cap;
+    auto take = [&](size_t bytes) { char* q = p; p += align256(bytes); return q; };
+    x.m = reinterpret_cast<double*>(take(ldn * 8));
+    x.ps = reinterpret_cast<double*>(take(ldn * 8));
+    x.pc = reinterpret_cast<double*>(take(ldn * 8));
+    x.D = reinterpret_cast<double*>(take(ldn * 8));
+    x.xstar = reinterpret_cast<double*>(take(ldn * 8));
+    x.lamdiag = reinterpret_cast<double*>(take(ldn * 8));
+    x.best_x = reinterpret_cast<double*>(take(ldn * 8));
+    x.yw = reinterpret_cast<double*>(take(ldn * 8));
+    x.zw = reinterpret_cast<double*>(take(ldn * 8));
+    x.w = reinterpret_cast<double*>(take(static_cast<size_t>(x.mu_cap) * 8));
+    x.hist = reinterpret_cast<double*>(take(static_cast<size_t>(x.hist_cap) * 8));
+    x.part = reinterpret_cast<double*>(take(static_cast<size_t>(part_doubles(x.n, x.ldn, x.mu_cap)) * 8));
+    x.C = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.B = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.BD = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.Q = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.EA = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.ET = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    x.Z = reinterpret_cast<double*>(take(ldn * lc * 8));
+    x.Y = reinterpret_cast<double*>(take(ldn * lc * 8));
+    x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
+    x.U = reinterpret_cast<double*>(take(ldn * lc * 8));
+    x.f = reinterpret_cast<double*>(take(lc * 8));
+    x.order = reinterpret_cast<int*>(take(lc * 4));
+    x.rank = reinterpret_cast<int*>(take(lc * 4));
+    CREATE_TRY(cudaMemcpyAsync(x.m, x0[s], n_ * 8, cudaMemcpyHostToDevice, h->stream));
+  }
+  CREATE_TRY(cudaMalloc(&h->dS, sizeof(Search) * count));
+  CREATE_TRY(cudaMemcpyAsync(h->dS, h->hs.data(), sizeof(Search) * count, cudaMemcpyHostToDevice, h->stream));
+  // tile prefix sums per kind
+  h->h_off.assign(static_cast<size_t>(TK_COUNT) * (count + 1), 0);
+  for (int k = 0; k < TK_COUNT; ++k) {
+    int* o = h->h_off.data() + static_cast<size_t>(k) * (count + 1);
+    long long acc = 0;
+    for (int s = 0; s < count; ++s) {
+      const Search& x = h->hs[s];
+      int t = 0;
+      switch (k) {
+        case TK_SAMPLE_Z: t = tiles_sample_z(x.n, x.lam_cap); break;
+        case TK_PANEL: t = tiles_gemm_panel(x.n, x.lam_cap); break;
+        case TK_COLRED: t = tiles_colreduce(x.lam_cap); break;
+        case TK_RANK: t = tiles_rank(x.lam_cap); break;
+        case TK_ROWS: t = tiles_rows(x.n); break;
+        case TK_RECOMB: t = tiles_recomb(x.n, x.mu_cap); break;
+        case TK_GEMV: t = tiles_gemv(x.n); break;
+        case TK_SYM: t = tiles_sym(x.n); break;
+        case TK_SQUARE: t = tiles_square(x.n); break;
+      }
+      o[s] = static_cast<int>(acc);
+      acc += t;
+    }
+    if (acc > 0x7fffffff) {
+      set_error(h, CMAES_EINVAL, "tile count overflow");
+      return fail(CMAES_EINVAL);
+    }
+    o[count] = static_cast<int>(acc);
+  }
+  CREATE_TRY(cudaMalloc(&h->d_off, sizeof(int) * h->h_off.size()));
+  CREATE_TRY(cudaMemcpyAsync(h->d_off, h->h_off.data(), sizeof(int) * h->h_off.size(), cudaMemcpyHostToDevice,
+                             h->stream));
+  launch_init_params(h->dS, 0, count, h->dopt, 1, h->stream);
+  h->launches += 1;
+  CREATE_TRY(cudaGetLastError());
+  CREATE_TRY(cudaStreamSynchronize(h->stream));
+  h->ask_pending.assign(count, 0);
+  *out = h;
+  return CMAES_OK;
+#undef CREATE_TRY
+}
+
+cmaes_status cmaes_create(int n, int lambda, const double* x0, double sigma0, uint64_t seed,
+                          const cmaes_options* opt, cmaes_t* out) {
+  const double* xs[1] = {x0};
+  return cmaes_create_batch(1, &n, &lambda, xs, &sigma0, seed, opt, out);
+}
+
+int cmaes_count(cmaes_t h) { return h ? h->count : 0; }
+
+cmaes_status cmaes_set_problem(cmaes_t h, int s, int kind, const double* Q, const double* lambda_diag,
+                               const double* xstar) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (kind < CMAES_OBJ_ELLIPSOID || kind > CMAES_OBJ_SPHERE)
+    return set_error(h, CMAES_EINVAL, "unknown objective kind %d", kind);
+  if (!xstar) return set_error(h, CMAES_EINVAL, "xstar is NULL");
+  if (kind != CMAES_OBJ_SPHERE && !Q) return set_error(h, CMAES_EINVAL, "Q is NULL");
+  if (kind == CMAES_OBJ_ELLIPSOID && !lambda_diag) return set_error(h, CMAES_EINVAL, "lambda_diag is NULL");
+  Search& x = h->hs[s];
+  const size_t n = x.n, ldn = x.ldn;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  CUDA_TRY(h, cudaMemcpy(x.xstar, xstar, n * 8, cudaMemcpyHostToDevice));
+  if (Q) CUDA_TRY(h, cudaMemcpy2D(x.Q, ldn * 8, Q, n * 8, n * 8, n, cudaMemcpyHostToDevice));
+  if (lambda_diag) CUDA_TRY(h, cudaMemcpy(x.lamdiag, lambda_diag, n * 8, cudaMemcpyHostToDevice));
+  x.obj = kind;
+  CUDA_TRY(h, cudaMemcpy(&h->dS[s].obj, &x.obj, sizeof(int), cudaMemcpyHostToDevice));
+  h->any_rotated = false;
+  for (const Search& y : h->hs)
+    if (y.obj == CMAES_OBJ_ELLIPSOID || y.obj == CMAES_OBJ_RASTRIGIN) h->any_rotated = true;
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream) {
+  CHECK_HANDLE(h);
+  if (generations < 0) return set_error(h, CMAES_EINVAL, "generations < 0");
+  for (int s = 0; s < h->count; ++s) {
+    if (h->hs[s].obj == CMAES_OBJ_NONE) return set_error(h, CMAES_EINVAL, "search %d has no objective", s);
+    if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d has an ask pending", s);
+  }
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  if (st != h->stream) {
+    // order this call after earlier work on the handle's own stream
+    cudaEvent_t ev;
+    CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventRecord(ev, h->stream));
+    CUDA_TRY(h, cudaStreamWaitEvent(st, ev, 0));
+    CUDA_TRY(h, cudaEventDestroy(ev));
+  }
+  for (int g = 0; g < generations; ++g) {
+    cmaes_status r = enqueue_generation(h, 0, h->count, st, true);
+    if (r != CMAES_OK) return r;
+  }
+  if (st != h->stream) {
+    cudaEvent_t ev;
+    CUDA_TRY(h, cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    CUDA_TRY(h, cudaEventRecord(ev, st));
+    CUDA_TRY(h, cudaStreamWaitEvent(h->stream, ev, 0));
+    CUDA_TRY(h, cudaEventDestroy(ev));
+  }
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_sync(cmaes_t h) {
+  CHECK_HANDLE(h);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_ask_device(cmaes_t h, int s, const double** X_dev, int* ld) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: ask pending, call tell first", s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  if (cur.done) return set_error(h, CMAES_ESTATE, "search %d is done", s);
+  enqueue_sample(h, s, s + 1, h->stream);
+  if ((r = launch_check(h, "sample")) != CMAES_OK) return r;
+  h->ask_pending[s] = 1;
+  if (X_dev) *X_dev = h->hs[s].X;
+  if (ld) *ld = h->hs[s].ldn;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_ask(cmaes_t h, int s, double* X_host) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (!X_host) return set_error(h, CMAES_EINVAL, "X_host is NULL");
+  cmaes_status r = cmaes_ask_device(h, s, nullptr, nullptr);
+  if (r != CMAES_OK) return r;
+  Search cur;
+  if ((r = read_search(h, s, &cur)) != CMAES_OK) return r;
+  const Search& x = h->hs[s];
+  CUDA_TRY(h, cudaMemcpy2D(X_host, static_cast<size_t>(x.n) * 8, x.X, static_cast<size_t>(x.ldn) * 8,
+                           static_cast<size_t>(x.n) * 8, cur.lam, cudaMemcpyDeviceToHost));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_tell(cmaes_t h, int s, const double* f_host) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (!f_host) return set_error(h, CMAES_EINVAL, "f_host is NULL");
+  if (!h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: tell without ask", s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  CUDA_TRY(h, cudaMemcpy(h->hs[s].f, f_host, static_cast<size_t>(cur.lam) * 8, cudaMemcpyHostToDevice));
+  if ((r = enqueue_generation(h, s, s + 1, h->stream, false)) != CMAES_OK) return r;
+  h->ask_pending[s] = 0;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_restart(cmaes_t h, int s) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: ask pending", s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  if (cur.done) return set_error(h, CMAES_ESTATE, "search %d is done", s);
+  if (h->dopt.ipop_double && static_cast<long long>(cur.lam) * 2 > h->hs[s].lam_cap)
+    return set_error(h, CMAES_ESTATE, "search %d: restart budget exhausted", s);
+  launch_force_restart(h->dS, s, h->dopt, h->stream);
+  h->launches += 1;
+  if ((r = launch_check(h, "restart")) != CMAES_OK) return r;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_best(cmaes_t h, int s, double* x, double* f) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  if (f) *f = cur.best_f;
+  if (x) CUDA_TRY(h, cudaMemcpy(x, h->hs[s].best_x, static_cast<size_t>(cur.n) * 8, cudaMemcpyDeviceToHost));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_query(cmaes_t h, int s, int* lambda, int* gen, int* restart, int* flags, int* done) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  if (lambda) *lambda = cur.lam;
+  if (gen) *gen = cur.gen;
+  if (restart) *restart = cur.restart;
+  if (flags) *flags = cur.flags;
+  if (done) *done = cur.done;
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_get_generation(cmaes_t h, int s, double* X, double* f, int* order) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  const Search& x = h->hs[s];
+  const size_t n = x.n, lam = cur.lam;
+  if (X) CUDA_TRY(h, cudaMemcpy2D(X, n * 8, x.X, static_cast<size_t>(x.ldn) * 8, n * 8, lam, cudaMemcpyDeviceToHost));
+  if (f) CUDA_TRY(h, cudaMemcpy(f, x.f, lam * 8, cudaMemcpyDeviceToHost));
+  if (order) CUDA_TRY(h, cudaMemcpy(order, x.order, lam * 4, cudaMemcpyDeviceToHost));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_get_state(cmaes_t h, int s, cmaes_state* st) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (!st) return set_error(h, CMAES_EINVAL, "state is NULL");
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  const Search& x = h->hs[s];
+  const size_t n = x.n, ldn = x.ldn;
+  st->n = x.n;
+  st->lambda = cur.lam;
+  st->gen = cur.gen;
+  st->restart = cur.restart;
+  st->done = cur.done;
+  st->flags = cur.flags;
+  st->sigma = cur.sigma;
+  st->best_f = cur.best_f;
+  const int cnt = cur.hist_count < cur.hist_len ? cur.hist_count : cur.hist_len;
+  st->hist_count = cnt;
+  if (st->m) CUDA_TRY(h, cudaMemcpy(st->m, x.m, n * 8, cudaMemcpyDeviceToHost));
+  if (st->ps) CUDA_TRY(h, cudaMemcpy(st->ps, x.ps, n * 8, cudaMemcpyDeviceToHost));
+  if (st->pc) CUDA_TRY(h, cudaMemcpy(st->pc, x.pc, n * 8, cudaMemcpyDeviceToHost));
+  if (st->D) CUDA_TRY(h, cudaMemcpy(st->D, x.D, n * 8, cudaMemcpyDeviceToHost));
+  if (st->best_x) CUDA_TRY(h, cudaMemcpy(st->best_x, x.best_x, n * 8, cudaMemcpyDeviceToHost));
+  if (st->C) CUDA_TRY(h, cudaMemcpy2D(st->C, n * 8, x.C, ldn * 8, n * 8, n, cudaMemcpyDeviceToHost));
+  if (st->B) CUDA_TRY(h, cudaMemcpy2D(st->B, n * 8, x.B, ldn * 8, n * 8, n, cudaMemcpyDeviceToHost));
+  if (st->hist && cnt > 0) {
+    std::vector<double> ring(cur.hist_len);
+    CUDA_TRY(h, cudaMemcpy(ring.data(), x.hist, static_cast<size_t>(cur.hist_len) * 8, cudaMemcpyDeviceToHost));
+    const int start = cur.hist_count <= cur.hist_len ? 0 : cur.hist_count % cur.hist_len;
+    for (int q = 0; q < cnt; ++q) st->hist[q] = ring[(start + q) % cur.hist_len];
+  }
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_set_state(cmaes_t h, int s, const cmaes_state* st) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  if (!st) return set_error(h, CMAES_EINVAL, "state is NULL");
+  const Search& x = h->hs[s];
+  if (st->n != x.n) return set_error(h, CMAES_EINVAL, "state n=%d does not match search n=%d", st->n, x.n);
+  if (st->lambda < x.lam0 || st->lambda > x.lam_cap)
+    return set_error(h, CMAES_EINVAL, "lambda=%d outside [%d, %d]", st->lambda, x.lam0, x.lam_cap);
+  if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: ask pending", s);
+  if (st->gen < 0 || st->restart < 0 || st->restart > 255 || !(st->sigma > 0.0))
+    return set_error(h, CMAES_EINVAL, "bad gen, restart or sigma");
+  const int hist_len = 10 + static_cast<int>(std::ceil(30.0 * x.n / st->lambda));
+  if (st->hist_count < 0 || (st->hist_count > 0 && !st->hist))
+    return set_error(h, CMAES_EINVAL, "bad hist");
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  const size_t n = x.n, ldn = x.ldn;
+  cur.lam = st->lambda;
+  cur.gen = st->gen;
+  cur.restart = st->restart;
+  cur.done = st->done;
+  cur.flags = st->flags;
+  cur.sigma = st->sigma;
+  cur.best_f = st->best_f;
+  cur.eig_due = 0;
+  const int keep = st->hist_count < hist_len ? st->hist_count : hist_len;
+  cur.hist_count = keep;
+  if (keep > 0) {
+    CUDA_TRY(h, cudaMemcpy(x.hist, st->hist + (st->hist_count - keep), static_cast<size_t>(keep) * 8,
+                           cudaMemcpyHostToDevice));
+  }
+  if ((r = write_search(h, s, &cur)) != CMAES_OK) return r;
+  if (st->m) CUDA_TRY(h, cudaMemcpy(x.m, st->m, n * 8, cudaMemcpyHostToDevice));
+  if (st->ps) CUDA_TRY(h, cudaMemcpy(x.ps, st->ps, n * 8, cudaMemcpyHostToDevice));
+  if (st->pc) CUDA_TRY(h, cudaMemcpy(x.pc, st->pc, n * 8, cudaMemcpyHostToDevice));
+  if (st->D) CUDA_TRY(h, cudaMemcpy(x.D, st->D, n * 8, cudaMemcpyHostToDevice));
+  if (st->best_x) CUDA_TRY(h, cudaMemcpy(x.best_x, st->best_x, n * 8, cudaMemcpyHostToDevice));
+  if (st->C) CUDA_TRY(h, cudaMemcpy2D(x.C, ldn * 8, st->C, n * 8, n * 8, n, cudaMemcpyHostToDevice));
+  if (st->B) CUDA_TRY(h, cudaMemcpy2D(x.B, ldn * 8, st->B, n * 8, n * 8, n, cudaMemcpyHostToDevice));
+  launch_init_params(h->dS, s, s + 1, h->dopt, 0, h->stream);
+  h->launches += 1;
+  TileMap sq = h->tiles(TK_SQUARE, s, s + 1);
+  launch_set_bd_force(h->dS, sq, h->stream);
+  h->launches += 1;
+  if ((r = launch_check(h, "set_state")) != CMAES_OK) return r;
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_set_profiling(cmaes_t h, int enable) {
+  CHECK_HANDLE(h);
+  if (!enable) {
+    cmaes_status r = drain_events(h);
+    if (r != CMAES_OK) return r;
+  }
+  h->profiling = enable != 0;
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches, int reset) {
+  CHECK_HANDLE(h);
+  cmaes_status r = drain_events(h);
+  if (r != CMAES_OK) return r;
+  for (int k = 0; k < kNumPhases; ++k) {
+    if (ms) ms[k] = h->phase_ms[k];
+    if (launches) launches[k] = h->phase_launch[k];
+  }
+  if (reset) {
+    for (int k = 0; k < kNumPhases; ++k) {
+      h->phase_ms[k] = 0.0;
+      h->phase_launch[k] = 0;
+    }
+  }
+  return CMAES_OK;
+}
+
+long long cmaes_kernel_launches(cmaes_t h) { return h ? h->launches : 0; }
+
+}  // extern "C"

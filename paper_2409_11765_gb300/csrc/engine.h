@@ -1,0 +1,104 @@
+// engine.h -- device data layout and kernel launchers of the batched engine.
+//
+// Every search owns a slice of one device arena. Vectors are padded to
+// ldn = round_up(n, 16) doubles; matrices are ldn x n column-major; population
+// panels are ldn x lam_cap column-major (one candidate per column), so a
+// column starts on a 128-byte boundary.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace cmaes_gb300 {
+
+constexpr int kPhaseSample = 0;
+constexpr int kPhaseObjective = 1;
+constexpr int kPhaseUpdate = 2;
+constexpr int kPhaseCov = 3;
+constexpr int kPhaseEig = 4;
+constexpr int kPhaseStop = 5;
+constexpr int kNumPhases = 6;
+
+// Options shared by all searches of one handle (passed by value to kernels).
+struct DevOptions {
+  int max_restarts;
+  int ipop_double;
+  int eig_every;
+  int max_iter;
+  int stop_mask;
+  int precision;
+  double f_target;
+  double box_lo, box_hi;
+  double tol_hist_fun, tol_x_factor, cond_max;
+  uint32_t key0, key1;  // Philox key (seed)
+};
+
+// Per-search descriptor, resident in device memory. Constant part first,
+// then the scalars that the kernels update every generation.
+struct Search {
+  // --- constant after create ---
+  int n, ldn, lam0, lam_cap, mu_cap, hist_cap, index, obj;
+  double sigma0;
+  double *m, *ps, *pc, *D, *xstar, *lamdiag, *best_x, *yw, *zw, *w, *hist;
+  double *part;                      // partial sums of the two-stage reductions
+  double *C, *B, *BD, *Q, *EA, *ET;  // ldn x n (EA, ET: eigensolver scratch)
+  double *Z, *Y, *X, *U, *f;         // ldn x lam_cap (f: lam_cap)
+  int *order, *rank;                 // lam_cap
+  // --- mutable ---
+  double sigma, best_f, mueff, cs, ds, cc, c1, cmu, chin, psnorm, hsig;
+  int lam, mu, gen, restart, g_eig, hist_len, max_iter, hist_count;
+  int done, flags, eig_due, eig_sweeps, pad_;
+};
+
+// Flattened tiles of one kernel over a contiguous range of searches:
+// tile t of the launch belongs to search s when off[s] <= t + off[s0] < off[s+1].
+struct TileMap {
+  const int* off;  // device, count + 1 prefix sums
+  int s0, s1;      // search range [s0, s1)
+  int total;       // off[s1] - off[s0]
+};
+
+// tile counts (host-side helpers, also used for prefix arrays)
+__host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; }
+int tiles_sample_z(int n, int lam_cap);
+int tiles_gemm_panel(int n, int lam_cap);   // 64 x 64 tiles of an n x lam panel
+int tiles_colreduce(int lam_cap);
+int tiles_rank(int lam_cap);
+int tiles_rows(int n);                      // 256-row blocks
+int tiles_recomb(int n, int mu_cap);        // 32 rows x 256 ranks
+int tiles_gemv(int n);                      // 32 rows x 256 columns
+int part_doubles(int n, int ldn, int mu_cap);
+int tiles_sym(int n);                       // upper 64 x 64 tiles of n x n
+int tiles_square(int n);                    // all 64 x 64 tiles of n x n
+
+enum TileKind {
+  TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
+  TK_COUNT
+};
+
+// launchers (kernels_gen.cu)
+void launch_init_params(Search* S, int s0, int s1, DevOptions o, int reset_state, cudaStream_t st);
+void launch_sample_z(Search* S, TileMap tm, DevOptions o, cudaStream_t st);
+void launch_gemm_sample(Search* S, TileMap tm, cudaStream_t st);
+void launch_gemm_objective(Search* S, TileMap tm, cudaStream_t st);
+void launch_colreduce_f(Search* S, TileMap tm, cudaStream_t st);
+void launch_rank(Search* S, TileMap tm, cudaStream_t st);
+void launch_recomb_partial(Search* S, TileMap tm, cudaStream_t st);
+void launch_recomb_final(Search* S, TileMap tm, cudaStream_t st);
+void launch_psigma_partial(Search* S, TileMap tm, cudaStream_t st);
+void launch_psigma_final(Search* S, TileMap tm, cudaStream_t st);
+void launch_finalize(Search* S, int s0, int s1, DevOptions o, cudaStream_t st);
+void launch_cov(Search* S, TileMap tm, cudaStream_t st);
+void launch_stop(Search* S, int s0, int s1, DevOptions o, cudaStream_t st);
+void launch_force_restart(Search* S, int s, DevOptions o, cudaStream_t st);
+// launchers (kernels_eig.cu)
+void launch_eig_gemm_CB(Search* S, TileMap tm, cudaStream_t st);
+void launch_eig_gemm_BtT(Search* S, TileMap tm, cudaStream_t st);
+// smem = true: one CTA per search with A and B in shared memory, for searches
+// with n <= jacobi_smem_max_n(); smem = false: the others, on global memory.
+void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int max_n, cudaStream_t st);
+void launch_set_bd(Search* S, TileMap tm, cudaStream_t st);
+void launch_set_bd_force(Search* S, TileMap tm, cudaStream_t st);
+int jacobi_smem_max_n();
+int jacobi_smem_bytes(int n, bool smem_mats);
+
+}  // namespace cmaes_gb300

@@ -1,0 +1,299 @@
+// kernels_eig.cu -- lazy FP64 eigendecomposition C = B D^2 B^T (§2.1).
+//
+// The paper calls LAPACK's dsyev on the main process (§3.1). Here the
+// decomposition is a warm-started parallel cyclic Jacobi method in FP64:
+//   1. A = B^T C B with the previous eigenbasis B. Between two decompositions
+//      C moves by O(c1 + c_mu), so A is nearly diagonal and few sweeps remain.
+//   2. Round-robin (tournament) ordering: each step rotates N/2 disjoint
+//      pairs (p, q) at once, chosen so that every pair meets once per sweep.
+//      The rotation zeroing a_pq uses theta = (a_qq - a_pp) / (2 a_pq),
+//      t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(1 + t^2),
+//      s = t c (Golub & Van Loan, §8.5), and is skipped when
+//      |a_pq| <= tol sqrt(|a_pp a_qq|) (a relative threshold).
+//   3. A <- J^T A J is applied per 2 x 2 block (pair P rows, pair Q columns);
+//      only blocks with P <= Q are computed and mirrored, so A stays
+//      symmetric. B <- B J accumulates the rotations into the eigenbasis.
+//   4. Sweeps repeat until one applies no rotation; then D^2 = diag(A), a PD
+//      guard lifts eigenvalues below max * 1e-16, and BD = B diag(D).
+// Small n keeps A and B in shared memory (one CTA per search); larger n runs
+// the same steps on the global-memory copies.
+#include <cmath>
+#include "device_common.cuh"
+
+namespace cmaes_gb300 {
+
+constexpr int kJacobiNT = 512;
+constexpr double kJacobiTol = 1e-14;
+constexpr int kJacobiMaxSweeps = 40;
+constexpr double kPdFloor = 1e-16;
+
+int jacobi_smem_bytes(int n, bool smem_mats) {
+  const int N = n + (n & 1), P = N / 2;
+  const int mats = smem_mats ? 2 * (N + 1) * N * 8 : 0;
+  return mats + P * (3 * 8 + 3 * 4) + 16;
+}
+
+int jacobi_smem_max_n() {
+  int best = 0;
+  for (int n = 2; n <= 256; n += 2)
+    if (jacobi_smem_bytes(n, true) <= 227 * 1024) best = n;
+  return best;
+}
+
+// ET = C B (square tiles; only searches whose decomposition is due).
+__global__ void __launch_bounds__(256) k_eig_gemm_CB(Search* S, TileMap tm) {
+  __shared__ GemmSmem sm;
+  int t;
+  const int si = find_search(tm, t);
+  const Search& s = S[si];
+  if (s.done || !s.eig_due) return;
+  const int n = s.n, ldn = s.ldn, T = ceil_div(n, kGBM);
+  const double* C = s.C;
+  const double* B = s.B;
+  double* ET = s.ET;
+  gemm_tile_f64<true, true>(
+      n, n, n, (t % T) * kGBM, (t / T) * kGBN,
+      [=] __device__(int i, int k) { return C[i + static_cast<long long>(ldn) * k]; },
+      [=] __device__(int k, int j) { return B[k + static_cast<long long>(ldn) * j]; },
+      [=] __device__(int i, int j, double acc) { ET[i + static_cast<long long>(ldn) * j] = acc; }, sm);
+}
+
+// EA = B^T ET = B^T C B.
+__global__ void __launch_bounds__(256) k_eig_gemm_BtT(Search* S, TileMap tm) {
+  __shared__ GemmSmem sm;
+  int t;
+  const int si = find_search(tm, t);
+  const Search& s = S[si];
+  if (s.done || !s.eig_due) return;
+  const int n = s.n, ldn = s.ldn, T = ceil_div(n, kGBM);
+  const double* B = s.B;
+  const double* ET = s.ET;
+  double* EA = s.EA;
+  gemm_tile_f64<false, true>(
+      n, n, n, (t % T) * kGBM, (t / T) * kGBN,
+      [=] __device__(int i, int k) { return B[k + static_cast<long long>(ldn) * i]; },
+      [=] __device__(int k, int j) { return ET[k + static_cast<long long>(ldn) * j]; },
+      [=] __device__(int i, int j, double acc) { EA[i + static_cast<long long>(ldn) * j] = acc; }, sm);
+}
+
+void launch_eig_gemm_CB(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_eig_gemm_CB<<<tm.total, 256, 0, st>>>(S, tm);
+}
+void launch_eig_gemm_BtT(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_eig_gemm_BtT<<<tm.total, 256, 0, st>>>(S, tm);
+}
+
+// Pair i of round-robin step r over N players (player N-1 fixed).
+__device__ __forceinline__ void rr_pair(int r, int i, int N, int& p, int& q) {
+  const int M = N - 1;
+  if (i == 0) {
+    p = r;
+    q = M;
+  } else {
+    p = (r + i) % M;
+    q = (r - i + M) % M;
+  }
+}
+
+template <bool SMEM>
+__global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int smem_max_n) {
+  extern __shared__ double dsm[];
+  __shared__ double shr[32];
+  __shared__ int sh_active;
+  Search& s = S[s0 + blockIdx.x];
+  if (s.done || !s.eig_due) return;
+  const int n = s.n, ldn = s.ldn;
+  if (SMEM != (n <= smem_max_n)) return;
+  const int N = n + (n & 1), P = N / 2;
+  const int tid = threadIdx.x;
+  double *A, *V;
+  long long lda;
+  double* rc;
+  if (SMEM) {
+    lda = N + 1;
+    A = dsm;
+    V = dsm + lda * N;
+    rc = V + lda * N;
+  } else {
+    lda = ldn;
+    A = s.EA;
+    V = s.B;
+    rc = dsm;
+  }
+  double* rsn = rc + P;
+  double* rtn = rsn + P;
+  int* rp = reinterpret_cast<int*>(rtn + P);
+  int* rq = rp + P;
+  int* ra = rq + P;
+
+  // symmetrised A = (EA + EA^T) / 2; V = B
+  if (SMEM) {
+    for (int e = tid; e < N * N; e += kJacobiNT) {
+      const int i = e % N, j = e / N;
+      double a = 0.0, v = 0.0;
+      if (i < n && j < n) {
+        a = 0.5 * (s.EA[i + static_cast<long long>(ldn) * j] + s.EA[j + static_cast<long long>(ldn) * i]);
+        v = s.B[i + static_cast<long long>(ldn) * j];
+      }
+      A[i + lda * j] = a;
+      V[i + lda * j] = v;
+    }
+  } else {
+    for (long long e = tid; e < static_cast<long long>(n) * n; e += kJacobiNT) {
+      const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
+      if (i < j) {
+        const double a = 0.5 * (A[i + lda * j] + A[j + lda * i]);
+        A[i + lda * j] = a;
+        A[j + lda * i] = a;
+      }
+    }
+  }
+  __syncthreads();
+
+  int sweeps = 0;
+  for (; sweeps < kJacobiMaxSweeps; ++sweeps) {
+    if (tid == 0) sh_active = 0;
+    __syncthreads();
+    for (int r = 0; r < N - 1; ++r) {
+      // rotations of this step
+      for (int i = tid; i < P; i += kJacobiNT) {
+        int p, q;
+        rr_pair(r, i, N, p, q);
+        double c = 1.0, sn = 0.0, tn = 0.0;
+        int act = 0;
+        if (p < n && q < n) {
+          const double app = A[p + lda * p], aqq = A[q + lda * q], apq = A[p + lda * q];
+          if (apq != 0.0 && fabs(apq) > kJacobiTol * sqrt(fabs(app * aqq))) {
+            const double theta = (aqq - app) / (2.0 * apq);
+            const double at = fabs(theta);
+            tn = (at > 1e150) ? 0.5 / theta : (theta >= 0.0 ? 1.0 : -1.0) / (at + sqrt(theta * theta + 1.0));
+            c = 1.0 / sqrt(tn * tn + 1.0);
+            sn = tn * c;
+            act = 1;
+          }
+        }
+        rc[i] = c;
+        rsn[i] = sn;
+        rtn[i] = tn;
+        rp[i] = p;
+        rq[i] = q;
+        ra[i] = act;
+        if (act) sh_active = 1;
+      }
+      __syncthreads();
+      // A <- J^T A J per 2x2 block (P <= Q), mirrored
+      const int nblk = P * (P + 1) / 2;
+      for (int b = tid; b < nblk; b += kJacobiNT) {
+        // row-major enumeration of the upper triangle of the P x P block grid
+        int bp = static_cast<int>((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+        while ((bp + 1) * (bp + 2) / 2 <= b) ++bp;
+        while (bp * (bp + 1) / 2 > b) --bp;
+        // b = bp (bp + 1) / 2 + bq', map to (P_idx = bq', Q_idx = bp) with P_idx <= Q_idx
+        const int bq = b - bp * (bp + 1) / 2;
+        const int Pi = bq, Qi = bp;
+        const int aP = ra[Pi], aQ = ra[Qi];
+        if (!aP && !aQ) continue;
+        const int p1 = rp[Pi], q1 = rq[Pi], p2 = rp[Qi], q2 = rq[Qi];
+        if (Pi == Qi) {
+          const double app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
+          const double t = rtn[Pi];
+          A[p1 + lda * p1] = app - t * apq;
+          A[q1 + lda * q1] = aqq + t * apq;
+          A[p1 + lda * q1] = 0.0;
+          A[q1 + lda * p1] = 0.0;
+          continue;
+        }
+        const double cP = rc[Pi], sP = rsn[Pi], cQ = rc[Qi], sQ = rsn[Qi];
+        const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
+        const double a = (vp1 && vp2) ? A[p1 + lda * p2] : 0.0;
+        const double bb = (vp1 && vq2) ? A[p1 + lda * q2] : 0.0;
+        const double c = (vq1 && vp2) ? A[q1 + lda * p2] : 0.0;
+        const double d = (vq1 && vq2) ? A[q1 + lda * q2] : 0.0;
+        const double y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
+        const double y10 = c * cQ - d * sQ, y11 = c * sQ + d * cQ;
+        const double x00 = cP * y00 - sP * y10, x01 = cP * y01 - sP * y11;
+        const double x10 = sP * y00 + cP * y10, x11 = sP * y01 + cP * y11;
+        if (vp1 && vp2) { A[p1 + lda * p2] = x00; A[p2 + lda * p1] = x00; }
+        if (vp1 && vq2) { A[p1 + lda * q2] = x01; A[q2 + lda * p1] = x01; }
+        if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
+        if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
+      }
+      // V <- V J for the active pairs
+      for (long long e = tid; e < static_cast<long long>(P) * n; e += kJacobiNT) {
+        const int pi = static_cast<int>(e / n), row = static_cast<int>(e % n);
+        if (!ra[pi]) continue;
+        const int p = rp[pi], q = rq[pi];
+        const double c = rc[pi], sn = rsn[pi];
+        const double vp = V[row + lda * p], vq = V[row + lda * q];
+        V[row + lda * p] = c * vp - sn * vq;
+        V[row + lda * q] = sn * vp + c * vq;
+      }
+      __syncthreads();
+    }
+    const int any = sh_active;
+    __syncthreads();
+    if (!any) break;
+  }
+
+  // eigenvalues, PD guard, D; B from V
+  double lo = INFINITY, hi = -INFINITY;
+  for (int i = tid; i < n; i += kJacobiNT) {
+    const double ev = A[i + lda * i];
+    lo = fmin(lo, ev);
+    hi = fmax(hi, ev);
+  }
+  hi = block_max<kJacobiNT>(hi, shr);
+  lo = -block_max<kJacobiNT>(-lo, shr);
+  const double add = (lo < hi * kPdFloor) ? hi * kPdFloor - lo : 0.0;
+  for (int i = tid; i < n; i += kJacobiNT) {
+    s.D[i] = sqrt(A[i + lda * i] + add);
+    if (add != 0.0) s.C[i + static_cast<long long>(ldn) * i] += add;
+  }
+  if (SMEM) {
+    for (int e = tid; e < n * n; e += kJacobiNT) {
+      const int i = e % n, j = e / n;
+      s.B[i + static_cast<long long>(ldn) * j] = V[i + lda * j];
+    }
+  }
+  if (tid == 0) s.eig_sweeps = sweeps + 1;
+}
+
+// Both variants cover the whole search range; each skips the searches that
+// belong to the other one.
+void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int max_n, cudaStream_t st) {
+  if (s1 <= s0) return;
+  const int bytes = jacobi_smem_bytes(max_n, smem);
+  if (smem) {
+    cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_jacobi<true><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, jacobi_smem_max_n());
+  } else {
+    cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_jacobi<false><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, jacobi_smem_max_n());
+  }
+}
+
+// BD = B diag(D); force = 1 applies to every search (after set_state).
+__global__ void __launch_bounds__(256) k_set_bd(Search* S, TileMap tm, int force) {
+  int t;
+  const int si = find_search(tm, t);
+  const Search& s = S[si];
+  if (s.done || !(force || s.eig_due)) return;
+  const int n = s.n, ldn = s.ldn, T = ceil_div(n, 64);
+  const int i0 = (t % T) * 64, j0 = (t / T) * 64;
+  for (int e = threadIdx.x; e < 64 * 64; e += 256) {
+    const int i = i0 + (e & 63), j = j0 + (e >> 6);
+    if (i < n && j < n) {
+      const long long x = i + static_cast<long long>(ldn) * j;
+      s.BD[x] = s.B[x] * s.D[j];
+    }
+  }
+}
+
+void launch_set_bd(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_set_bd<<<tm.total, 256, 0, st>>>(S, tm, 0);
+}
+void launch_set_bd_force(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_set_bd<<<tm.total, 256, 0, st>>>(S, tm, 1);
+}
+
+}  // namespace cmaes_gb300
