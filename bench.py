@@ -1,0 +1,335 @@
+#!/usr/bin/env python3
+"""Throughput of the batched CMA-ES generation loop on GB300.
+
+Workload (default): the IPOP-CMA-ES configuration on the rotated Rastrigin,
+n = 100, lambda0 = 17 with population levels 17 * 2^k for k = 0..9 (lambda up
+to 8704), laid out as the paper's K-Distributed strategy (§3.2.3): the ten
+levels run side by side as one batch of ten searches, each restarting at its
+own size when a stop test fires. One step = one generation of every search =
+17391 candidates sampled, evaluated and used in the update (rank,
+recombination, paths, step size, rank-one + rank-mu covariance update), plus
+the lazy FP64 eigendecomposition when due (every generation here) and the
+stop tests. Inputs are seeded synthetic instances (no BBOB data).
+
+Prints one JSON line (rank 0). Timing: W warm-up generations, then K timed
+generations, each bracketed by CUDA events on the launch stream, with a
+256 MiB write between timed generations to flush L2. Per-phase device times
+come from CUDA events the engine records on the same stream.
+
+--impl reference times the FP64 CPU oracle on this host's cores on the same
+workload (test infrastructure; it is the method's plain restatement).
+"""
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "candidates/sec sampled+evaluated+updated; mixed vs plain FP64 GPU; % roofline"
+UNIT = "candidates/s"
+
+
+def parse_args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=200)
+    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--e2e-steps", type=int, default=50)
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    return ap.parse_args()
+
+
+def dist_env():
+    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
+            int(os.environ.get("WORLD_SIZE", "1")))
+
+
+def workload():
+    from paper_2409_11765_gb300 import workloads as W
+    return W.rastrigin_n100_ipop(concurrent=True)
+
+
+def workload_config(wl, precision):
+    s0 = wl.searches[0]
+    return {"workload": wl.name, "searches": len(wl.searches), "n": s0.n,
+            "lambdas": [s.lam for s in wl.searches],
+            "candidates_per_step": wl.candidates_per_generation,
+            "objective": "rotated Rastrigin (seeded Haar Q, x* ~ U[-4,4]^n)",
+            "layout": "K-Distributed: levels lambda=17*2^k, k=0..9, one batch",
+            "precision": precision, "eig": "FP64 warm-started Jacobi, every generation (lazy rule gives 1)",
+            "l2": "256 MiB write between timed generations", "seed": 20240918}
+
+
+# ----------------------------- CPU oracle ----------------------------------
+def oracle_searches(wl):
+    from oracle import cmaes
+    sts, probs = [], []
+    for s in wl.searches:
+        sts.append(cmaes.State(s.n, s.lam, s.sigma0, s.x0.copy(), s.sigma0))
+        p = s.problem
+        probs.append(cmaes.Problem(p.kind, p.xstar, p.Q, p.lamdiag))
+    opts = cmaes.Options(f_target=wl.f_target, box_lo=wl.box_lo, box_hi=wl.box_hi,
+                         max_restarts=wl.max_restarts if wl.max_restarts < 255 else 10 ** 9,
+                         ipop_double=wl.ipop_double)
+    return sts, probs, opts
+
+
+def oracle_step(sts, probs, opts):
+    from oracle import cmaes
+    from paper_2409_11765_gb300 import workloads as W
+    cand = 0
+    for i, (st, pr) in enumerate(zip(sts, probs)):
+        if not st.done:
+            cand += st.lam
+            cmaes.generation(st, W.SEED, i, pr, opts)
+    return cand
+
+
+def cpu_baseline(wl, seconds):
+    """The oracle as it stands, on this host's cores, for a bounded sample of
+    generations of the same batch."""
+    sts, probs, opts = oracle_searches(wl)
+    t0 = time.perf_counter()
+    cand = 0
+    gens = 0
+    while True:
+        cand += oracle_step(sts, probs, opts)
+        gens += 1
+        el = time.perf_counter() - t0
+        if el >= seconds and gens >= 2:
+            break
+    return {"value": cand / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+            "sample": "%d generations of the full 10-search batch (%d candidates) in %.1f s; "
+                      "numpy FP64, BLAS threads = host cores" % (gens, cand, el)}
+
+
+def run_reference(args):
+    rank, _, world = dist_env()
+    if rank != 0:
+        return
+    wl = workload()
+    sts, probs, opts = oracle_searches(wl)
+    for _ in range(args.warmup):
+        oracle_step(sts, probs, opts)
+    t0 = time.perf_counter()
+    cand = 0
+    for _ in range(args.steps):
+        cand += oracle_step(sts, probs, opts)
+    el = time.perf_counter() - t0
+    value = cand / el
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": workload_config(wl, "fp64"),
+            "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
+                             "kind": "oracle",
+                             "sample": "%d timed generations of the full batch" % args.steps},
+            "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ------------------------------- clocks -------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index):
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(gpu_index),
+                                       "--query-gpu=" + self.QUERY, "--format=csv,noheader,nounits",
+                                       "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.flush()
+        self.f.seek(0)
+        rows = [r.split(",") for r in self.f.read().strip().splitlines() if r.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            r = [x.strip() for x in r]
+            if len(r) < 9:
+                continue
+            try:
+                sm.append(float(r[1]))
+                smax.append(float(r[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, r[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------ GPU engine ----------------------------------
+def eig_flops(n, rotations, decompositions):
+    """Algorithmic FP64 flops of the eigendecomposition: B^T (C B) as two
+    n x n x n products (4 n^3 per decomposition) plus 12 n per plane rotation
+    (6 n on the symmetric A: two rows/columns of 3-flop updates; 6 n on the
+    two columns of B)."""
+    return 4.0 * n ** 3 * decompositions + 12.0 * n * rotations
+
+
+def run_engine(args):
+    import torch
+    rank, local_rank, world = dist_env()
+    torch.cuda.set_device(local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
+
+    import paper_2409_11765_gb300 as eng
+    from paper_2409_11765_gb300 import _build
+    if rank == 0 or world == 1:
+        _build.build()
+    if dist is not None:
+        dist.barrier()
+
+    wl = workload()
+    count = len(wl.searches)
+    opt = eng.cmaes_default_options(f_target=wl.f_target, box_lo=wl.box_lo, box_hi=wl.box_hi,
+                                    max_restarts=255, ipop_double=0)
+    ns = [s.n for s in wl.searches]
+    h = eng.cmaes_create_batch(ns, [s.lam for s in wl.searches], [s.x0 for s in wl.searches],
+                               [s.sigma0 for s in wl.searches], 20240918 + 7919 * rank, opt)
+    for i, s in enumerate(wl.searches):
+        p = s.problem
+        eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
+
+    stream = torch.cuda.current_stream()
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    for _ in range(args.warmup):
+        eng.cmaes_step_batch(h, 1, sptr)
+    torch.cuda.synchronize()
+
+    eig0 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
+    eng.cmaes_phase_times(h, reset=True)
+    eng.cmaes_set_profiling(h, True)
+    launches0 = eng.cmaes_kernel_launches(h)
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank] \
+        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local_rank)
+    sampler = ClockSampler(gpu_index)
+    time.sleep(0.3)
+    if dist is not None:
+        dist.barrier()
+    torch.cuda.synchronize()
+    wall0 = time.perf_counter()
+    for k in range(args.steps):
+        flush.fill_(k & 255)
+        starts[k].record(stream)
+        eng.cmaes_step_batch(h, 1, sptr)
+        ends[k].record(stream)
+    torch.cuda.synchronize()
+    if dist is not None:
+        dist.barrier()
+    wall = time.perf_counter() - wall0
+    clocks = sampler.stop()
+    launches = eng.cmaes_kernel_launches(h) - launches0
+    eng.cmaes_set_profiling(h, False)
+    phase_ms, phase_launch = eng.cmaes_phase_times(h, reset=True)
+    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
+    if dist is not None:
+        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+    cand_step = wl.candidates_per_generation
+    value = cand_step * args.steps * world / (total_ms / 1e3)
+
+    eig1 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
+    dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
+    rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
+    swp = sum(b["sweeps"] - a["sweeps"] for a, b in zip(eig0, eig1))
+
+    # e2e through the public API: one generation + a host read of every
+    # search's best point and value, synchronised each step
+    import numpy as np
+    e2e_t0 = time.perf_counter()
+    for _ in range(args.e2e_steps):
+        eng.cmaes_step_batch(h, 1)
+        for i in range(count):
+            eng.cmaes_best(h, i, ns[i])
+    e2e_el = time.perf_counter() - e2e_t0
+    e2e_value = cand_step * args.e2e_steps * world / e2e_el
+    d2h = sum(8 * n + 8 for n in ns)
+
+    # roofline of the dominant phase
+    fp64_peak = eng.probe_fma_tflops(64)
+    dom = max(phase_ms, key=phase_ms.get)
+    n = ns[0]
+    lam_sum = cand_step
+    mu_sum = sum(s.lam // 2 for s in wl.searches)
+    phase_flops = {
+        "sample": 2.0 * lam_sum * n * n,
+        "objective": 2.0 * lam_sum * n * n,
+        "cov": 1.0 * mu_sum * n * (n + 1) + 3.0 * count * n * n,
+        "eig": eig_flops(n, rot, dec) / args.steps,
+        "update": 2.0 * count * n * n + 4.0 * mu_sum * n,
+        "stop": 0.0,
+    }
+    dom_ms = phase_ms[dom] / args.steps
+    achieved = phase_flops[dom] / (dom_ms * 1e-3) / 1e12
+    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
+                "frac": achieved / fp64_peak, "traffic": None,
+                "kernel": dom, "peak_source": "FP64 DFMA probe measured live on this GPU",
+                "algorithmic_flops_per_step": phase_flops[dom]}
+    eng.cmaes_destroy(h)
+
+    if rank != 0:
+        return
+    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": workload_config(wl, args.precision), "roofline": roofline,
+            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": d2h},
+            "gpu_launches": int(launches), "clocks": clocks,
+            "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+            "eig_ms_per_step": phase_ms["eig"] / args.steps,
+            "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot},
+            "wall_s_timed_loop": wall}
+    if not args.no_cpu_baseline and world == 1:
+        line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
+    print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def main():
+    args = parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_engine(args)
+
+
+if __name__ == "__main__":
+    main()

@@ -207,6 +207,12 @@ cmaes_status cmaes_set_profiling(cmaes_t h, int enable);
 cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches,
                                int reset);
 
+/* Work done by the eigensolver of search s since creation: decompositions,
+ * Jacobi sweeps and plane rotations applied (any pointer may be NULL).
+ * Synchronises. */
+cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions,
+                             long long* sweeps, long long* rotations);
+
 /* Number of kernel launches issued by the handle since creation. */
 long long cmaes_kernel_launches(cmaes_t h);
 

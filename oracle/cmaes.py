@@ -184,8 +184,20 @@ def eig_due(st, prm, opts):
     return st.gen % every == 0
 
 
+def canonical_basis(B):
+    """Sign convention of the eigenvectors: §2.1 only asks for orthonormal
+    eigenvectors, so the representative is fixed by making each column's
+    entry of largest magnitude (the first on ties) positive. Columns come in
+    ascending eigenvalue order from the solver."""
+    B = B.copy()
+    idx = np.argmax(np.abs(B), axis=0)
+    sign = np.where(B[idx, np.arange(B.shape[1])] < 0.0, -1.0, 1.0)
+    return B * sign[None, :]
+
+
 def eig_step(st):
-    """B, D from the eigendecomposition of C (§2.1), with a PD guard."""
+    """B, D from the eigendecomposition of C (§2.1), with a PD guard; columns
+    in ascending eigenvalue order with the sign of canonical_basis."""
     n = st.n
     C = 0.5 * (st.C + st.C.T)
     evals, evecs = np.linalg.eigh(C)
@@ -196,7 +208,7 @@ def eig_step(st):
         C = C + add * np.eye(n)
         evals = evals + add
     st.C = C
-    st.B = evecs
+    st.B = canonical_basis(evecs)
     st.D = np.sqrt(evals)
 
 

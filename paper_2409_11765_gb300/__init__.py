@@ -20,7 +20,8 @@ __all__ = [
     "cmaes_create_batch", "cmaes_count", "cmaes_set_problem", "cmaes_ask", "cmaes_ask_device",
     "cmaes_tell", "cmaes_step_batch", "cmaes_sync", "cmaes_restart", "cmaes_best",
     "cmaes_get_state", "cmaes_set_state", "cmaes_get_generation", "cmaes_query",
-    "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_strerror",
+    "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
+    "probe_fma_tflops", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
 
@@ -100,6 +101,9 @@ def lib():
         "cmaes_set_profiling": (I, [H, I]),
         "cmaes_phase_times": (I, [H, _DP, ctypes.POINTER(ctypes.c_longlong), I]),
         "cmaes_kernel_launches": (ctypes.c_longlong, [H]),
+        "cmaes_eig_stats": (I, [H, I, ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong),
+                                ctypes.POINTER(ctypes.c_longlong)]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
         "cmaes_destroy": (None, [H]),
@@ -290,6 +294,25 @@ def cmaes_phase_times(h, reset=False):
     ln = (ctypes.c_longlong * 6)()
     _check(h, lib().cmaes_phase_times(h, ms, ln, 1 if reset else 0))
     return dict(zip(PHASES, ms)), dict(zip(PHASES, ln))
+
+
+def cmaes_eig_stats(h, s):
+    v = [ctypes.c_longlong() for _ in range(3)]
+    _check(h, lib().cmaes_eig_stats(h, s, *[ctypes.byref(x) for x in v]))
+    return dict(zip(("decompositions", "sweeps", "rotations"), (x.value for x in v)))
+
+
+def probe_fma_tflops(precision=64, blocks_per_sm=4, repeats=5):
+    """Measured FMA throughput of the current device (TFLOP/s)."""
+    L = ctypes.CDLL(_build.PROBE_LIB)
+    L.cmaes_probe_fma_tflops.restype = ctypes.c_int
+    L.cmaes_probe_fma_tflops.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                         ctypes.POINTER(ctypes.c_double)]
+    out = ctypes.c_double()
+    st = L.cmaes_probe_fma_tflops(precision, blocks_per_sm, repeats, ctypes.byref(out))
+    if st != 0:
+        raise CmaesError(st, "FMA probe failed")
+    return out.value
 
 
 def cmaes_kernel_launches(h):

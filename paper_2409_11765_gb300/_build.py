@@ -8,6 +8,7 @@ CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(PKG, "_build")
 LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcmaes_gb300.so")
+PROBE_LIB = os.path.join(LIBDIR, "libcmaes_probe.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 SOURCES = ["kernels_gen.cu", "kernels_eig.cu", "capi.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
@@ -24,30 +25,36 @@ def _nvcc():
 
 def _deps():
     files = [os.path.join(CSRC, f) for f in os.listdir(CSRC)]
-    files.append(os.path.join(INCLUDE, "cmaes.h"))
+    files += [os.path.join(INCLUDE, f) for f in os.listdir(INCLUDE)]
     return files
 
 
 def up_to_date():
-    if not os.path.exists(LIB):
+    if not (os.path.exists(LIB) and os.path.exists(PROBE_LIB)):
         return False
-    t = os.path.getmtime(LIB)
+    t = min(os.path.getmtime(LIB), os.path.getmtime(PROBE_LIB))
     return all(os.path.getmtime(f) <= t for f in _deps())
 
 
 def build(force=False, verbose=False):
-    """Compile the CUDA sources in parallel and link libcmaes_gb300.so."""
+    """Compile the CUDA sources in parallel and link libcmaes_gb300.so and
+    libcmaes_probe.so."""
     if not force and up_to_date():
         return LIB
     os.makedirs(BUILD, exist_ok=True)
     os.makedirs(LIBDIR, exist_ok=True)
     nvcc = _nvcc()
-    procs = []
+    jobs = []
     objs = []
     for src in SOURCES:
         obj = os.path.join(BUILD, src.replace(".cu", ".o"))
         objs.append(obj)
-        cmd = [nvcc, *FLAGS, *ARCH, "-I", INCLUDE, "-c", os.path.join(CSRC, src), "-o", obj]
+        jobs.append((src, [nvcc, *FLAGS, *ARCH, "-I", INCLUDE, "-c", os.path.join(CSRC, src),
+                           "-o", obj]))
+    jobs.append(("probe.cu", [nvcc, *FLAGS, *ARCH, "-I", INCLUDE, "-shared", "-o",
+                              PROBE_LIB + ".tmp", os.path.join(CSRC, "probe.cu")]))
+    procs = []
+    for src, cmd in jobs:
         if verbose:
             print(" ".join(cmd), file=sys.stderr)
         procs.append((src, subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)))
@@ -58,6 +65,7 @@ def build(force=False, verbose=False):
             errors.append("%s:\n%s" % (src, out.decode(errors="replace")))
     if errors:
         raise RuntimeError("nvcc failed\n" + "\n".join(errors))
+    os.replace(PROBE_LIB + ".tmp", PROBE_LIB)
     tmp = LIB + ".tmp"
     cmd = [nvcc, "-shared", *ARCH, "-o", tmp, *objs, "-lcudart"]
     r = subprocess.run(cmd, stdout=subprocess.PIPE, stderr=subprocess.STDOUT)

@@ -754,6 +754,19 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches, int r
   return CMAES_OK;
 }
 
+cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions, long long* sweeps,
+                             long long* rotations) {
+  CHECK_HANDLE(h);
+  CHECK_SEARCH(h, s);
+  Search cur;
+  cmaes_status r = read_search(h, s, &cur);
+  if (r != CMAES_OK) return r;
+  if (decompositions) *decompositions = cur.eig_count;
+  if (sweeps) *sweeps = cur.eig_sweeps_total;
+  if (rotations) *rotations = cur.eig_rotations;
+  return CMAES_OK;
+}
+
 long long cmaes_kernel_launches(cmaes_t h) { return h ? h->launches : 0; }
 
 }  // extern "C"

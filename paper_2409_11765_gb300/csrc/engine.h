@@ -47,6 +47,8 @@ struct Search {
   double sigma, best_f, mueff, cs, ds, cc, c1, cmu, chin, psnorm, hsig;
   int lam, mu, gen, restart, g_eig, hist_len, max_iter, hist_count;
   int done, flags, eig_due, eig_sweeps, pad_;
+  // eigensolver work counters (decompositions, sweeps, rotations applied)
+  long long eig_count, eig_sweeps_total, eig_rotations;
 };
 
 // Flattened tiles of one kernel over a contiguous range of searches:

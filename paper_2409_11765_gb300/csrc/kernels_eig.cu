@@ -15,6 +15,10 @@
 //      symmetric. B <- B J accumulates the rotations into the eigenbasis.
 //   4. Sweeps repeat until one applies no rotation; then D^2 = diag(A), a PD
 //      guard lifts eigenvalues below max * 1e-16, and BD = B diag(D).
+//   5. The paper only asks for "a matrix containing orthonormal eigenvectors";
+//      the representative is fixed here so that any two solvers agree: columns
+//      in ascending eigenvalue order (ties by index) and each column's entry of
+//      largest magnitude (first on ties) positive.
 // Small n keeps A and B in shared memory (one CTA per search); larger n runs
 // the same steps on the global-memory copies.
 #include <cmath>
@@ -30,7 +34,7 @@ constexpr double kPdFloor = 1e-16;
 int jacobi_smem_bytes(int n, bool smem_mats) {
   const int N = n + (n & 1), P = N / 2;
   const int mats = smem_mats ? 2 * (N + 1) * N * 8 : 0;
-  return mats + P * (3 * 8 + 3 * 4) + 16;
+  return mats + P * (3 * 8 + 3 * 4) + N * (2 * 8 + 4) + 16;
 }
 
 int jacobi_smem_max_n() {
@@ -100,6 +104,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
   extern __shared__ double dsm[];
   __shared__ double shr[32];
   __shared__ int sh_active;
+  __shared__ long long sh_rot;
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due) return;
   const int n = s.n, ldn = s.ldn;
@@ -117,14 +122,17 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
   } else {
     lda = ldn;
     A = s.EA;
-    V = s.B;
+    V = s.ET;  // free once EA = B^T (C B) is formed; B is rewritten at the end
     rc = dsm;
   }
   double* rsn = rc + P;
   double* rtn = rsn + P;
-  int* rp = reinterpret_cast<int*>(rtn + P);
+  double* ev = rtn + P;
+  double* sg = ev + N;
+  int* rp = reinterpret_cast<int*>(sg + N);
   int* rq = rp + P;
   int* ra = rq + P;
+  int* rk = ra + P;
 
   // symmetrised A = (EA + EA^T) / 2; V = B
   if (SMEM) {
@@ -146,10 +154,12 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
         A[i + lda * j] = a;
         A[j + lda * i] = a;
       }
+      V[i + lda * j] = s.B[i + static_cast<long long>(ldn) * j];
     }
   }
   __syncthreads();
 
+  if (tid == 0) sh_rot = 0;
   int sweeps = 0;
   for (; sweeps < kJacobiMaxSweeps; ++sweeps) {
     if (tid == 0) sh_active = 0;
@@ -178,7 +188,10 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
         rp[i] = p;
         rq[i] = q;
         ra[i] = act;
-        if (act) sh_active = 1;
+        if (act) {
+          sh_active = 1;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sh_rot), 1ull);
+        }
       }
       __syncthreads();
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
@@ -235,27 +248,59 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
     if (!any) break;
   }
 
-  // eigenvalues, PD guard, D; B from V
+  // eigenvalues with the PD guard
   double lo = INFINITY, hi = -INFINITY;
   for (int i = tid; i < n; i += kJacobiNT) {
-    const double ev = A[i + lda * i];
-    lo = fmin(lo, ev);
-    hi = fmax(hi, ev);
+    const double e = A[i + lda * i];
+    lo = fmin(lo, e);
+    hi = fmax(hi, e);
   }
   hi = block_max<kJacobiNT>(hi, shr);
   lo = -block_max<kJacobiNT>(-lo, shr);
   const double add = (lo < hi * kPdFloor) ? hi * kPdFloor - lo : 0.0;
   for (int i = tid; i < n; i += kJacobiNT) {
-    s.D[i] = sqrt(A[i + lda * i] + add);
+    ev[i] = A[i + lda * i] + add;
     if (add != 0.0) s.C[i + static_cast<long long>(ldn) * i] += add;
   }
-  if (SMEM) {
-    for (int e = tid; e < n * n; e += kJacobiNT) {
-      const int i = e % n, j = e / n;
-      s.B[i + static_cast<long long>(ldn) * j] = V[i + lda * j];
-    }
+  __syncthreads();
+  // canonical representative: rank by ascending eigenvalue (ties by index) ...
+  for (int i = tid; i < n; i += kJacobiNT) {
+    const double e = ev[i];
+    int r = 0;
+    for (int j = 0; j < n; ++j) r += (ev[j] < e) || (ev[j] == e && j < i);
+    rk[i] = r;
   }
-  if (tid == 0) s.eig_sweeps = sweeps + 1;
+  // ... and the sign that makes the largest-magnitude entry positive
+  const int lane = tid & 31, warp = tid >> 5;
+  for (int j = warp; j < n; j += kJacobiNT / 32) {
+    double best = -1.0, val = 0.0;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      const double v = V[i + lda * j], a = fabs(v);
+      if (a > best) { best = a; val = v; bi = i; }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) { best = ob; val = ov; bi = oi; }
+    }
+    if (lane == 0) sg[j] = (val < 0.0) ? -1.0 : 1.0;
+  }
+  __syncthreads();
+  for (int i = tid; i < n; i += kJacobiNT) s.D[rk[i]] = sqrt(ev[i]);
+  for (long long e = tid; e < static_cast<long long>(n) * n; e += kJacobiNT) {
+    const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
+    s.B[i + static_cast<long long>(ldn) * rk[j]] = sg[j] * V[i + lda * j];
+  }
+  if (tid == 0) {
+    const int done_sweeps = sweeps < kJacobiMaxSweeps ? sweeps + 1 : sweeps;
+    s.eig_sweeps = done_sweeps;
+    s.eig_count += 1;
+    s.eig_sweeps_total += done_sweeps;
+    s.eig_rotations += sh_rot;
+  }
 }
 
 // Both variants cover the whole search range; each skips the searches that

@@ -115,10 +115,19 @@ def check_generation(gpu, ora, tol=TOL_FP64, eig=True):
         assert rel(g["best_x"], st.best_x) <= tol
     B, D = g["B"], g["D"]
     if eig:
-        ev_g, ev_o = np.sort(D ** 2), np.sort(st.D ** 2)
+        ev_g, ev_o = D ** 2, st.D ** 2
+        assert np.all(np.diff(ev_g) >= 0), "eigenvalues not ascending"
         assert np.abs(ev_g - ev_o).max() <= tol * ev_o.max(), ("D", np.abs(ev_g - ev_o).max())
         assert np.abs(B.T @ B - np.eye(n)).max() <= 1e-13 * max(n, 10)
         recon = (B * D ** 2) @ B.T
         assert rel(recon, g["C"]) <= tol, ("BD^2B^T", rel(recon, g["C"]))
+        # eigenvectors: same canonical representative, to within the
+        # conditioning of each one (relative gap to its neighbours)
+        for j in range(n):
+            others = np.delete(ev_o, j)
+            gap = np.min(np.abs(others - ev_o[j])) / ev_o.max() if n > 1 else 1.0
+            if gap > 1e-6:
+                err = np.abs(B[:, j] - st.B[:, j]).max()
+                assert err <= 1e-13 / gap + 1e-13, ("B column", j, err, gap)
     else:
         assert rel(B, st.B) == 0.0 and rel(D, st.D) == 0.0

@@ -9,14 +9,15 @@ import pytest
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def _declared():
-    names = set()
-    for fn in os.listdir(os.path.join(ROOT, "include")):
-        if fn.endswith(".h"):
-            text = open(os.path.join(ROOT, "include", fn)).read()
-            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"\b(cmaes_[a-z_]+)\s*\(", text))
-    return names
+def _declared(header="cmaes.h"):
+    text = open(os.path.join(ROOT, "include", header)).read()
+    text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+    return set(re.findall(r"\b(cmaes_[a-z_]+)\s*\(", text))
+
+
+def test_every_header_has_a_library():
+    headers = sorted(f for f in os.listdir(os.path.join(ROOT, "include")) if f.endswith(".h"))
+    assert headers == ["cmaes.h", "cmaes_probe.h"]
 
 
 @pytest.fixture(scope="module")
@@ -36,9 +37,13 @@ def test_header_declares_the_boundary():
 
 
 def test_library_exports_every_declared_symbol(libpath):
-    L = ctypes.CDLL(libpath)
-    missing = [n for n in sorted(_declared()) if not hasattr(L, n)]
-    assert not missing, missing
+    from paper_2409_11765_gb300 import _build
+    for header, path in (("cmaes.h", libpath), ("cmaes_probe.h", _build.PROBE_LIB)):
+        L = ctypes.CDLL(path)
+        names = _declared(header)
+        assert names
+        missing = [n for n in sorted(names) if not hasattr(L, n)]
+        assert not missing, (header, missing)
 
 
 def test_host_only_calls_without_gpu(libpath):

@@ -100,3 +100,22 @@ def test_objectives_special_points():
     assert objectives.rastrigin(x[:, None], pr.Q, pr.xstar)[0] == pytest.approx(5.0, abs=1e-10)
     # ellipsoid spectrum runs from 1 to cond
     assert pe.lamdiag[0] == 1.0 and math.isclose(pe.lamdiag[-1], 1e6, rel_tol=1e-14)
+
+
+def test_canonical_eigenbasis_is_unique():
+    """Any orthonormal eigenbasis (columns permuted, signs flipped) maps to the
+    same representative: ascending eigenvalues, largest entry positive."""
+    n = 8
+    d = W.random_state(n, 23, 1, cond=1e4)
+    st = cmaes.State(n, 10, 1.0, np.zeros(n), 1.0, C=d["C"].copy())
+    cmaes.eig_step(st)
+    assert np.all(np.diff(st.D) > 0)
+    B = st.B
+    idx = np.argmax(np.abs(B), axis=0)
+    assert np.all(B[idx, np.arange(n)] > 0)
+    rng = np.random.default_rng(0)
+    perm = rng.permutation(n)
+    flipped = (d["B"] * rng.choice([-1.0, 1.0], size=n))[:, perm]
+    order = np.argsort(d["D"][perm])
+    again = cmaes.canonical_basis(flipped[:, order])
+    assert np.allclose(again, B, atol=1e-10)
