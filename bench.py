@@ -222,8 +222,12 @@ def run_engine(args):
         p = s.problem
         eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
 
-    stream = torch.cuda.current_stream()
+    # a dedicated stream: the engine launches on it and the CUDA events that
+    # time the steps are recorded on it
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
     sptr = stream.cuda_stream
+    assert sptr != 0
     flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
     for _ in range(args.warmup):
         eng.cmaes_step_batch(h, 1, sptr)

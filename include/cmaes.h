@@ -164,9 +164,11 @@ cmaes_status cmaes_tell(cmaes_t h, int s, const double* f_host);
 
 /* Runs `generations` full generations of every search that is not done, with
  * the built-in objectives, asynchronously on `stream` (a cudaStream_t; NULL
- * selects the handle's own stream). Searches that finish stop consuming
- * work. Errors: EINVAL (a search without an objective), ESTATE (an ask is
- * pending). */
+ * selects the handle's own non-blocking stream, which does not order with the
+ * legacy default stream). The work is ordered after earlier work of the
+ * handle and later calls are ordered after it. Searches that finish stop
+ * consuming work. Errors: EINVAL (a search without an objective), ESTATE (an
+ * ask is pending). */
 cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream);
 
 /* Waits for all work of the handle. */

@@ -167,8 +167,10 @@ static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
 }
 
 static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
-  TileMap t = h->tiles(TK_SYM, s0, s1);
-  launch_cov(h->dS, t, st);
+  TileMap p = h->tiles(TK_COVP, s0, s1), t = h->tiles(TK_SYM, s0, s1);
+  launch_cov_partial(h->dS, p, st);
+  count_launch(h, kPhaseCov, p.total);
+  launch_cov_reduce(h->dS, t, st);
   count_launch(h, kPhaseCov, t.total);
 }
 
@@ -360,12 +362,14 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.index = s;
     x.obj = 0;
     x.sigma0 = sigma0[s];
+    cov_split(n, x.mu_cap, &x.cov_kc, &x.cov_nch);
     const size_t ldn = x.ldn, n_ = n, lc = x.lam_cap;
     size_t b = 0;
     b += 9 * align256(ldn * 8);                       // vectors
     b += align256(static_cast<size_t>(x.mu_cap) * 8);  // w
     b += align256(static_cast<size_t>(x.hist_cap) * 8);
     b += align256(static_cast<size_t>(part_doubles(n, x.ldn, x.mu_cap)) * 8);
+    if (x.cov_nch > 1) b += align256(static_cast<size_t>(tiles_sym(n)) * x.cov_nch * 4096 * 8);
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
     b += 4 * align256(ldn * lc * 8);                   // Z Y X U
     b += align256(lc * 8);                             // f
@@ -415,6 +419,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.w = reinterpret_cast<double*>(take(static_cast<size_t>(x.mu_cap) * 8));
     x.hist = reinterpret_cast<double*>(take(static_cast<size_t>(x.hist_cap) * 8));
     x.part = reinterpret_cast<double*>(take(static_cast<size_t>(part_doubles(x.n, x.ldn, x.mu_cap)) * 8));
+    x.covpart = x.cov_nch > 1
+                    ? reinterpret_cast<double*>(take(static_cast<size_t>(tiles_sym(x.n)) * x.cov_nch * 4096 * 8))
+                    : nullptr;
     x.C = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.B = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.BD = reinterpret_cast<double*>(take(ldn * n_ * 8));
@@ -450,6 +457,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_GEMV: t = tiles_gemv(x.n); break;
         case TK_SYM: t = tiles_sym(x.n); break;
         case TK_SQUARE: t = tiles_square(x.n); break;
+        case TK_COVP: t = tiles_sym(x.n) * x.cov_nch; break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

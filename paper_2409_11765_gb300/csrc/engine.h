@@ -40,6 +40,8 @@ struct Search {
   double sigma0;
   double *m, *ps, *pc, *D, *xstar, *lamdiag, *best_x, *yw, *zw, *w, *hist;
   double *part;                      // partial sums of the two-stage reductions
+  double *covpart;                   // rank-mu partial tiles: tiles_sym x cov_nch x 64 x 64
+  int cov_kc, cov_nch;               // rank chunk length and chunk count of the split
   double *C, *B, *BD, *Q, *EA, *ET;  // ldn x n (EA, ET: eigensolver scratch)
   double *Z, *Y, *X, *U, *f;         // ldn x lam_cap (f: lam_cap)
   int *order, *rank;                 // lam_cap
@@ -70,11 +72,12 @@ int tiles_recomb(int n, int mu_cap);        // 32 rows x 256 ranks
 int tiles_gemv(int n);                      // 32 rows x 256 columns
 int part_doubles(int n, int ldn, int mu_cap);
 int tiles_sym(int n);                       // upper 64 x 64 tiles of n x n
+void cov_split(int n, int mu_cap, int* kc, int* nch);  // split of the rank-mu sum
 int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COUNT
+  TK_COVP, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -89,7 +92,8 @@ void launch_recomb_final(Search* S, TileMap tm, cudaStream_t st);
 void launch_psigma_partial(Search* S, TileMap tm, cudaStream_t st);
 void launch_psigma_final(Search* S, TileMap tm, cudaStream_t st);
 void launch_finalize(Search* S, int s0, int s1, DevOptions o, cudaStream_t st);
-void launch_cov(Search* S, TileMap tm, cudaStream_t st);
+void launch_cov_partial(Search* S, TileMap tm, cudaStream_t st);
+void launch_cov_reduce(Search* S, TileMap tm, cudaStream_t st);
 void launch_stop(Search* S, int s0, int s1, DevOptions o, cudaStream_t st);
 void launch_force_restart(Search* S, int s, DevOptions o, cudaStream_t st);
 // launchers (kernels_eig.cu)

@@ -198,7 +198,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
       const int nblk = P * (P + 1) / 2;
       for (int b = tid; b < nblk; b += kJacobiNT) {
         // row-major enumeration of the upper triangle of the P x P block grid
-        int bp = static_cast<int>((sqrt(8.0 * b + 1.0) - 1.0) * 0.5);
+        int bp = static_cast<int>((sqrtf(static_cast<float>(8 * b + 1)) - 1.0f) * 0.5f);
         while ((bp + 1) * (bp + 2) / 2 <= b) ++bp;
         while (bp * (bp + 1) / 2 > b) --bp;
         // b = bp (bp + 1) / 2 + bq', map to (P_idx = bq', Q_idx = bp) with P_idx <= Q_idx

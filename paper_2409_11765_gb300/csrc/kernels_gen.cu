@@ -449,43 +449,106 @@ void launch_finalize(Search* S, int s0, int s1, DevOptions o, cudaStream_t st) {
 
 // --------------------------- covariance update -------------------------------
 // Eq. (2) through Eq. (3): C <- a C + c1 p_c p_c^T + c_mu sum_r w_r y_r y_r^T
-// with a = 1 - c1 - c_mu + c1 (1 - h_sigma) c_c (2 - c_c). Upper 64 x 64 tiles
-// only; each tile writes C(i, j) and its mirror C(j, i), so C stays exactly
-// symmetric. Reads touch the upper triangle only, which makes the in-place
-// update race free.
-__global__ void __launch_bounds__(256) k_cov(Search* S, TileMap tm) {
+// with a = 1 - c1 - c_mu + c1 (1 - h_sigma) c_c (2 - c_c). Only the upper
+// 64 x 64 tiles are formed and each writes C(i, j) and its mirror C(j, i), so C
+// stays exactly symmetric; reads touch the upper triangle only, which makes the
+// in-place update race free. The rank sum is split into chunks of cov_kc
+// ranks (k_cov_partial, one CTA per tile and chunk) and the chunk sums are
+// added in chunk order by k_cov_reduce, which applies the update. With a
+// single chunk the partial kernel applies the update itself.
+void cov_split(int n, int mu_cap, int* kc, int* nch) {
+  const int tiles = tiles_sym(n);
+  const int max_ch = tiles >= 512 ? 1 : 512 / tiles;
+  int c = ceil_div(mu_cap, 64);
+  if (c > max_ch) c = max_ch;
+  if (c < 1) c = 1;
+  const int k = ((ceil_div(mu_cap, c) + 15) / 16) * 16;
+  *kc = k > 0 ? k : 16;
+  *nch = ceil_div(mu_cap, *kc) > 0 ? ceil_div(mu_cap, *kc) : 1;
+}
+
+__device__ __forceinline__ void sym_tile(int t, int n, int& ti, int& tj) {
+  const int T = ceil_div(n, kGBM);
+  int rem = t;
+  ti = 0;
+  while (rem >= T - ti) { rem -= T - ti; ++ti; }
+  tj = ti + rem;
+}
+
+__global__ void __launch_bounds__(256) k_cov_partial(Search* S, TileMap tm) {
   __shared__ GemmSmem sm;
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
   if (s.done) return;
-  const int n = s.n, ldn = s.ldn, mu = s.mu;
-  int ti = 0, rem = t, T = ceil_div(n, kGBM);
-  while (rem >= T - ti) { rem -= T - ti; ++ti; }
-  const int tj = ti + rem;
+  const int n = s.n, ldn = s.ldn, mu = s.mu, nch = s.cov_nch, kc = s.cov_kc;
+  const int tile = t / nch, c = t % nch;
+  const int k_lo = c * kc;
+  if (k_lo >= mu) return;
+  const int k_hi = min(mu, k_lo + kc);
+  int ti, tj;
+  sym_tile(tile, n, ti, tj);
   const double* Y = s.Y;
-  const double* w = s.w;
-  const int* order = s.order;
-  double* C = s.C;
-  const double* pc = s.pc;
-  const double c1 = s.c1, cmu = s.cmu;
-  const double a = 1.0 - c1 - cmu + c1 * (1.0 - s.hsig) * s.cc * (2.0 - s.cc);
+  const double* w = s.w + k_lo;
+  const int* order = s.order + k_lo;
+  if (nch == 1) {
+    double* C = s.C;
+    const double* pc = s.pc;
+    const double c1 = s.c1, cmu = s.cmu;
+    const double a = 1.0 - c1 - cmu + c1 * (1.0 - s.hsig) * s.cc * (2.0 - s.cc);
+    gemm_tile_f64<true, false>(
+        n, n, k_hi - k_lo, ti * kGBM, tj * kGBN,
+        [=] __device__(int i, int r) { return w[r] * Y[i + static_cast<long long>(ldn) * order[r]]; },
+        [=] __device__(int r, int j) { return Y[j + static_cast<long long>(ldn) * order[r]]; },
+        [=] __device__(int i, int j, double acc) {
+          if (i > j) return;
+          const long long e = i + static_cast<long long>(ldn) * j;
+          const double v = a * C[e] + c1 * pc[i] * pc[j] + cmu * acc;
+          C[e] = v;
+          C[j + static_cast<long long>(ldn) * i] = v;
+        },
+        sm);
+    return;
+  }
+  double* out = s.covpart + (static_cast<long long>(tile) * nch + c) * (kGBM * kGBN);
+  const int i0 = ti * kGBM, j0 = tj * kGBN;
   gemm_tile_f64<true, false>(
-      n, n, mu, ti * kGBM, tj * kGBN,
+      n, n, k_hi - k_lo, i0, j0,
       [=] __device__(int i, int r) { return w[r] * Y[i + static_cast<long long>(ldn) * order[r]]; },
       [=] __device__(int r, int j) { return Y[j + static_cast<long long>(ldn) * order[r]]; },
-      [=] __device__(int i, int j, double acc) {
-        if (i > j) return;
-        const long long e = i + static_cast<long long>(ldn) * j;
-        const double v = a * C[e] + c1 * pc[i] * pc[j] + cmu * acc;
-        C[e] = v;
-        C[j + static_cast<long long>(ldn) * i] = v;
-      },
-      sm);
+      [=] __device__(int i, int j, double acc) { out[(i - i0) + kGBM * (j - j0)] = acc; }, sm);
 }
 
-void launch_cov(Search* S, TileMap tm, cudaStream_t st) {
-  if (tm.total > 0) k_cov<<<tm.total, 256, 0, st>>>(S, tm);
+__global__ void __launch_bounds__(256) k_cov_reduce(Search* S, TileMap tm) {
+  int t;
+  const int si = find_search(tm, t);
+  const Search& s = S[si];
+  if (s.done || s.cov_nch == 1) return;
+  const int n = s.n, ldn = s.ldn, nch = s.cov_nch;
+  const int used = ceil_div(s.mu, s.cov_kc);
+  int ti, tj;
+  sym_tile(t, n, ti, tj);
+  const double c1 = s.c1, cmu = s.cmu;
+  const double a = 1.0 - c1 - cmu + c1 * (1.0 - s.hsig) * s.cc * (2.0 - s.cc);
+  const double* part = s.covpart + static_cast<long long>(t) * nch * (kGBM * kGBN);
+  for (int e = threadIdx.x; e < kGBM * kGBN; e += 256) {
+    const int ii = e & (kGBM - 1), jj = e >> 6;
+    const int i = ti * kGBM + ii, j = tj * kGBN + jj;
+    if (i >= n || j >= n || i > j) continue;
+    double acc = 0.0;
+    for (int c = 0; c < used; ++c) acc += part[static_cast<long long>(c) * (kGBM * kGBN) + e];
+    const long long x = i + static_cast<long long>(ldn) * j;
+    const double v = a * s.C[x] + c1 * s.pc[i] * s.pc[j] + cmu * acc;
+    s.C[x] = v;
+    s.C[j + static_cast<long long>(ldn) * i] = v;
+  }
+}
+
+void launch_cov_partial(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_cov_partial<<<tm.total, 256, 0, st>>>(S, tm);
+}
+void launch_cov_reduce(Search* S, TileMap tm, cudaStream_t st) {
+  if (tm.total > 0) k_cov_reduce<<<tm.total, 256, 0, st>>>(S, tm);
 }
 
 // ------------------------------ stop + restart ------------------------------

@@ -157,11 +157,13 @@ def test_state_roundtrip():
 
 
 def test_small_ellipsoid_reaches_target():
-    """Plain CMA-ES, n=10, lambda=10, rotated ellipsoid cond 1e6: f < 1e-10
-    within 2000 generations, and the same trajectory as the oracle for the
-    first generations."""
+    """Plain CMA-ES, n=10, lambda=10, rotated ellipsoid cond 1e6, from the
+    configuration's own start: f < 1e-10 within 2000 generations, confirmed by
+    an FP64 re-evaluation of the returned point. (From C = I the first updates
+    leave C with a repeated eigenvalue, whose eigenvectors any solver may pick
+    differently, so this run is compared by outcome, not step by step.)"""
     import paper_2409_11765_gb300 as eng
-    from oracle import cmaes
+    from oracle import objectives
     from paper_2409_11765_gb300 import workloads as W
     wl = W.ellipsoid_n10()
     s = wl.searches[0]
@@ -170,20 +172,13 @@ def test_small_ellipsoid_reaches_target():
     try:
         p = s.problem
         eng.cmaes_set_problem(h, 0, p.kind, p.Q, p.lamdiag, p.xstar)
-        eng.cmaes_step_batch(h, 5)
-        g5 = eng.cmaes_get_state(h, 0, s.n)
-        eng.cmaes_step_batch(h, wl.generations - 5)
+        eng.cmaes_step_batch(h, wl.generations)
         q = eng.cmaes_query(h, 0)
         x, fbest = eng.cmaes_best(h, 0, s.n)
     finally:
         eng.cmaes_destroy(h)
-    st = cmaes.State(s.n, s.lam, s.sigma0, s.x0.copy(), s.sigma0)
-    opts = cmaes.Options(f_target=wl.f_target, max_restarts=0)
-    cmaes.run(st, SEED, 0, oracle_problem(p), opts, 5)
-    assert rel(g5["m"], st.m) < 1e-11 and rel(g5["C"], st.C) < 1e-11
     assert q["done"] == 1 and q["flags"] & 1
     assert fbest < 1e-10
-    from oracle import objectives
     f_re = objectives.evaluate(p.kind, x[:, None], p.Q, p.lamdiag, p.xstar)[0]
     assert f_re < 1e-10 and math.isclose(f_re, fbest, rel_tol=1e-6, abs_tol=1e-14)
 
@@ -219,27 +214,32 @@ def test_kdistributed_levels_full_batch():
         check_generation(gpu, ora)
 
 
-@pytest.mark.parametrize("n,lam,kind,gens", [(10, 10, 1, 12), (30, 20, 2, 10), (100, 17, 2, 6)])
+@pytest.mark.parametrize("n,lam,kind,gens", [(10, 10, 1, 25), (30, 20, 2, 20), (100, 17, 2, 10),
+                                             (100, 2176, 2, 6)])
 def test_trajectory_follows_oracle(n, lam, kind, gens):
-    """Several generations in a row, each with an eigendecomposition: the
-    canonical eigenbasis keeps the GPU and oracle trajectories together (the
-    dynamics amplify rounding differences only slowly over these spans)."""
+    """Many generations in a row, each with a warm-started eigendecomposition,
+    from a state whose eigenvalues are distinct: with the canonical eigenbasis
+    the GPU and oracle trajectories stay together (the dynamics amplify
+    rounding differences only slowly)."""
     import paper_2409_11765_gb300 as eng
     from oracle import cmaes
     from paper_2409_11765_gb300 import workloads as W
+    from parity_util import oracle_state, state_dict
     p = W.make_problem(kind, n, SEED, 300 + n)
-    x0 = W.start_point(n, -4, 4, SEED, 300 + n)
+    d = W.random_state(n, SEED, 300 + n, cond=1e2)
+    d["sigma"] = 1.0
     opt = eng.cmaes_default_options(eig_every=1, max_restarts=0)
-    h = eng.cmaes_create(n, lam, x0, 2.0, SEED, opt)
-    st = cmaes.State(n, lam, 2.0, x0.copy(), 2.0)
+    h = eng.cmaes_create(n, lam, d["m"], 2.0, SEED, opt)
+    st = oracle_state(d, n, lam, 2.0, gen=1)
     opts = cmaes.Options(eig_every=1, max_restarts=0)
     try:
         eng.cmaes_set_problem(h, 0, p.kind, p.Q, p.lamdiag, p.xstar)
+        eng.cmaes_set_state(h, 0, state_dict(d, n, lam, gen=1))
         for g in range(gens):
             eng.cmaes_step_batch(h, 1)
             cmaes.generation(st, SEED, 0, oracle_problem(p), opts)
             s = eng.cmaes_get_state(h, 0, n)
-            tol = 1e-12 * 10 ** (g / 4)
+            tol = 1e-12 * 10 ** (g / 5)
             assert rel(s["m"], st.m) < tol, (g, rel(s["m"], st.m))
             assert rel(s["C"], st.C) < tol, (g, rel(s["C"], st.C))
             assert abs(s["sigma"] / st.sigma - 1) < tol
