@@ -218,6 +218,39 @@ cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions,
 /* Number of kernel launches issued by the handle since creation. */
 long long cmaes_kernel_launches(cmaes_t h);
 
+/* Evaluates a built-in objective on lambda points without allocating any
+ * device memory. The paper has no counterpart: this serves callers that
+ * cannot call cudaMalloc at that point -- code whose device memory is managed
+ * by another component (a framework's caching allocator, a plug-in inside a
+ * host application) or loops where the latency and implicit synchronisation
+ * of an allocation are not acceptable. It computes the same f as the engine's
+ * objective phase, bit for bit.
+ *
+ *   kind         CMAES_OBJ_ELLIPSOID, _RASTRIGIN or _SPHERE
+ *   X            device, n x lambda column-major, leading dimension ld >= n
+ *   Q            device, n x n column-major, leading dimension ldq >= n
+ *                (not read for SPHERE; may be NULL then)
+ *   lambda_diag  device, n (ELLIPSOID only; may be NULL otherwise)
+ *   xstar        device, n
+ *   f            device, lambda doubles, written
+ *   stream       cudaStream_t the kernels are launched on (NULL: legacy default)
+ *
+ * The intermediate U = Q (X - x*) lives in one static device array of 2^20
+ * doubles (8 MiB) that every GPU loading the library keeps until the process
+ * exits; ld * lambda above 2^20 is rejected with CMAES_EINVAL (SPHERE needs no
+ * scratch and has no limit). All calls share that array: two calls whose
+ * kernels overlap on the GPU (different streams, or different threads on the
+ * same device) race and give wrong results. Nothing in it needs to start at
+ * zero. The first call on each device looks up the array's device address
+ * (cudaGetSymbolAddress, with that device current); make that first call
+ * before any stream capture. The call is asynchronous on `stream`; errors:
+ * EINVAL (arguments, size), ECUDA; the text is in cmaes_last_error(NULL). */
+cmaes_status cmaes_evaluate_noalloc(int kind, int n, int lambda, const double* X,
+                                    int ld, const double* Q, int ldq,
+                                    const double* lambda_diag,
+                                    const double* xstar, double* f,
+                                    void* stream);
+
 const char* cmaes_strerror(cmaes_status st);
 /* Text of the last error on h (or of the last failed create if h is NULL). */
 const char* cmaes_last_error(cmaes_t h);

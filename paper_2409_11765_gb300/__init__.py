@@ -21,7 +21,7 @@ __all__ = [
     "cmaes_tell", "cmaes_step_batch", "cmaes_sync", "cmaes_restart", "cmaes_best",
     "cmaes_get_state", "cmaes_set_state", "cmaes_get_generation", "cmaes_query",
     "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
-    "probe_fma_tflops", "cmaes_strerror",
+    "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
 
@@ -104,6 +104,7 @@ def lib():
         "cmaes_eig_stats": (I, [H, I, ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong),
                                 ctypes.POINTER(ctypes.c_longlong)]),
+        "cmaes_evaluate_noalloc": (I, [I, I, I, V, I, V, I, V, V, V, V]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
         "cmaes_destroy": (None, [H]),
@@ -317,6 +318,15 @@ def probe_fma_tflops(precision=64, blocks_per_sm=4, repeats=5):
 
 def cmaes_kernel_launches(h):
     return lib().cmaes_kernel_launches(h)
+
+
+def cmaes_evaluate_noalloc(kind, n, lam, X_ptr, ld, Q_ptr, ldq, lamdiag_ptr, xstar_ptr, f_ptr,
+                           stream=None):
+    """Objective values of lam points held in device memory (pointers as
+    ints), with no device allocation; see include/cmaes.h."""
+    st = lib().cmaes_evaluate_noalloc(kind, n, lam, X_ptr, ld, Q_ptr, ldq, lamdiag_ptr, xstar_ptr,
+                                      f_ptr, stream)
+    _check(None, st)
 
 
 def cmaes_strerror(st):

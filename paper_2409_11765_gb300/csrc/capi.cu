@@ -65,6 +65,8 @@ struct cmaes_s {
 
 static std::string g_create_error;
 
+void cmaes_gb300::set_global_error(const char* msg) { g_create_error = msg; }
+
 static cmaes_status set_error(cmaes_t h, cmaes_status st, const char* fmt, ...) {
   char buf[512];
   va_list ap;

@@ -107,4 +107,7 @@ void launch_set_bd_force(Search* S, TileMap tm, cudaStream_t st);
 int jacobi_smem_max_n();
 int jacobi_smem_bytes(int n, bool smem_mats);
 
+// Error text of calls that have no handle (read by cmaes_last_error(NULL)).
+void set_global_error(const char* msg);
+
 }  // namespace cmaes_gb300
