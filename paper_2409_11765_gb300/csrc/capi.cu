@@ -42,7 +42,7 @@ struct cmaes_s {
   cmaes_status err = CMAES_OK;
   std::string msg;
   std::vector<int> ask_pending;
-  int max_n = 0, max_n_smem_jacobi = 0, max_n_global_jacobi = 0;
+  int max_n = 0, max_n_small_jacobi = 0, max_n_cluster_jacobi = 0, max_n_global_jacobi = 0;
   bool any_rotated = false;
   long long launches = 0;
   // profiling
@@ -182,12 +182,16 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   count_launch(h, kPhaseEig, sq.total);
   launch_eig_gemm_BtT(h->dS, sq, st);
   count_launch(h, kPhaseEig, sq.total);
-  if (h->max_n_smem_jacobi > 0) {
-    launch_jacobi_variant(h->dS, s0, s1, true, h->max_n_smem_jacobi, st);
+  if (h->max_n_small_jacobi > 0) {
+    launch_jacobi_variant(h->dS, s0, s1, true, 0, kJacobiSmallN, h->max_n_small_jacobi, st);
+    count_launch(h, kPhaseEig, s1 - s0);
+  }
+  if (h->max_n_cluster_jacobi > 0) {
+    launch_jacobi_cluster(h->dS, s0, s1, kJacobiSmallN, kJacobiClusterN, h->max_n_cluster_jacobi, st);
     count_launch(h, kPhaseEig, s1 - s0);
   }
   if (h->max_n_global_jacobi > 0) {
-    launch_jacobi_variant(h->dS, s0, s1, false, h->max_n_global_jacobi, st);
+    launch_jacobi_variant(h->dS, s0, s1, false, kJacobiClusterN, 1 << 30, h->max_n_global_jacobi, st);
     count_launch(h, kPhaseEig, s1 - s0);
   }
   launch_set_bd(h->dS, sq, st);
@@ -343,7 +347,6 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   h->hs.resize(count);
   size_t total = 0;
   std::vector<size_t> base(count);
-  const int jmax = jacobi_smem_max_n();
   for (int s = 0; s < count; ++s) {
     const int n = n_arr[s];
     int lam = lam_arr ? lam_arr[s] : 0;
@@ -379,8 +382,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     base[s] = total;
     total += b;
     if (n > h->max_n) h->max_n = n;
-    if (n <= jmax) { if (n > h->max_n_smem_jacobi) h->max_n_smem_jacobi = n; }
-    else if (n > h->max_n_global_jacobi) h->max_n_global_jacobi = n;
+    int* jm = n <= kJacobiSmallN ? &h->max_n_small_jacobi
+              : n <= kJacobiClusterN ? &h->max_n_cluster_jacobi : &h->max_n_global_jacobi;
+    if (n > *jm) *jm = n;
   }
   h->arena_bytes = total;
   cudaError_t e = cudaMalloc(&h->arena, total);

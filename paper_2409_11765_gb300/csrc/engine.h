@@ -99,9 +99,14 @@ void launch_force_restart(Search* S, int s, DevOptions o, cudaStream_t st);
 // launchers (kernels_eig.cu)
 void launch_eig_gemm_CB(Search* S, TileMap tm, cudaStream_t st);
 void launch_eig_gemm_BtT(Search* S, TileMap tm, cudaStream_t st);
-// smem = true: one CTA per search with A and B in shared memory, for searches
-// with n <= jacobi_smem_max_n(); smem = false: the others, on global memory.
-void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int max_n, cudaStream_t st);
+// Jacobi variants by dimension: one CTA per search with A and B in shared
+// memory (n <= kJacobiSmallN), an 8-CTA cluster per search (kJacobiSmallN <
+// n <= kJacobiClusterN), one CTA per search on global memory (larger n).
+constexpr int kJacobiSmallN = 32;
+constexpr int kJacobiClusterN = 256;
+void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int lo_n, int hi_n, int max_n,
+                           cudaStream_t st);
+void launch_jacobi_cluster(Search* S, int s0, int s1, int lo_n, int hi_n, int layout_n, cudaStream_t st);
 void launch_set_bd(Search* S, TileMap tm, cudaStream_t st);
 void launch_set_bd_force(Search* S, TileMap tm, cudaStream_t st);
 int jacobi_smem_max_n();

@@ -100,7 +100,7 @@ __device__ __forceinline__ void rr_pair(int r, int i, int N, int& p, int& q) {
 }
 
 template <bool SMEM>
-__global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int smem_max_n) {
+__global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_n, int hi_n) {
   extern __shared__ double dsm[];
   __shared__ double shr[32];
   __shared__ int sh_active;
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due) return;
   const int n = s.n, ldn = s.ldn;
-  if (SMEM != (n <= smem_max_n)) return;
+  if (n <= lo_n || n > hi_n) return;
   const int N = n + (n & 1), P = N / 2;
   const int tid = threadIdx.x;
   double *A, *V;
@@ -303,17 +303,18 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int sme
   }
 }
 
-// Both variants cover the whole search range; each skips the searches that
-// belong to the other one.
-void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int max_n, cudaStream_t st) {
-  if (s1 <= s0) return;
+// Each launch covers the whole search range and processes the searches with
+// lo_n < n <= hi_n (A and B in shared memory needs hi_n <= jacobi_smem_max_n()).
+void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int lo_n, int hi_n, int max_n,
+                           cudaStream_t st) {
+  if (s1 <= s0 || max_n <= lo_n) return;
   const int bytes = jacobi_smem_bytes(max_n, smem);
   if (smem) {
     cudaFuncSetAttribute(k_jacobi<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_jacobi<true><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, jacobi_smem_max_n());
+    k_jacobi<true><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, lo_n, hi_n);
   } else {
     cudaFuncSetAttribute(k_jacobi<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_jacobi<false><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, jacobi_smem_max_n());
+    k_jacobi<false><<<s1 - s0, kJacobiNT, bytes, st>>>(S, s0, lo_n, hi_n);
   }
 }
 

@@ -35,7 +35,10 @@ def _states(ns, stream0=0, cond=1e3):
     (65, 130, 2),     # ragged 64-tiles in both GEMM dimensions
     (100, 17, 2),     # Rastrigin n = 100, lambda0 = 17
     (100, 1088, 1),   # several rank / recombination chunks
-    (130, 40, 1),     # n above the shared-memory Jacobi limit: global variant
+    (33, 20, 1),      # smallest cluster-Jacobi size: two CTAs of the cluster idle
+    (130, 40, 1),     # cluster Jacobi
+    (256, 30, 2),     # largest cluster-Jacobi size
+    (300, 40, 1),     # global-memory Jacobi
 ])
 def test_teacher_forced_generation(n, lam, kind):
     gpu, ora = teacher_forced([n], [lam], [kind], _states([n]), eig_every=1)
