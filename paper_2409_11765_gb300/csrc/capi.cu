@@ -153,8 +153,10 @@ static void enqueue_objective(cmaes_t h, int s0, int s1, cudaStream_t st) {
 
 static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap r = h->tiles(TK_RANK, s0, s1), rc = h->tiles(TK_RECOMB, s0, s1);
+  TileMap r2 = h->tiles(TK_RANK2D, s0, s1);
   TileMap rows = h->tiles(TK_ROWS, s0, s1), gv = h->tiles(TK_GEMV, s0, s1);
-  launch_rank(h->dS, r, st);
+  launch_rank(h->dS, r2, r, st);
+  count_launch(h, kPhaseUpdate, r2.total);
   count_launch(h, kPhaseUpdate, r.total);
   launch_recomb_partial(h->dS, rc, st);
   count_launch(h, kPhaseUpdate, rc.total);
@@ -464,6 +466,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_SYM: t = tiles_sym(x.n); break;
         case TK_SQUARE: t = tiles_square(x.n); break;
         case TK_COVP: t = tiles_sym(x.n) * x.cov_nch; break;
+        case TK_RANK2D: t = tiles_rank2d(x.lam_cap); break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

@@ -66,7 +66,9 @@ __host__ __device__ inline int ceil_div(int a, int b) { return (a + b - 1) / b; 
 int tiles_sample_z(int n, int lam_cap);
 int tiles_gemm_panel(int n, int lam_cap);   // 64 x 64 tiles of an n x lam panel
 int tiles_colreduce(int lam_cap);
+constexpr int kRankChunk = 1024;
 int tiles_rank(int lam_cap);
+int tiles_rank2d(int lam_cap);
 int tiles_rows(int n);                      // 256-row blocks
 int tiles_recomb(int n, int mu_cap);        // 32 rows x 256 ranks
 int tiles_gemv(int n);                      // 32 rows x 256 columns
@@ -77,7 +79,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -86,7 +88,7 @@ void launch_sample_z(Search* S, TileMap tm, DevOptions o, cudaStream_t st);
 void launch_gemm_sample(Search* S, TileMap tm, cudaStream_t st);
 void launch_gemm_objective(Search* S, TileMap tm, cudaStream_t st);
 void launch_colreduce_f(Search* S, TileMap tm, cudaStream_t st);
-void launch_rank(Search* S, TileMap tm, cudaStream_t st);
+void launch_rank(Search* S, TileMap tm2d, TileMap tm, cudaStream_t st);
 void launch_recomb_partial(Search* S, TileMap tm, cudaStream_t st);
 void launch_recomb_final(Search* S, TileMap tm, cudaStream_t st);
 void launch_psigma_partial(Search* S, TileMap tm, cudaStream_t st);

@@ -161,10 +161,14 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
 
   if (tid == 0) sh_rot = 0;
   int sweeps = 0;
-  for (; sweeps < kJacobiMaxSweeps; ++sweeps) {
-    if (tid == 0) sh_active = 0;
-    __syncthreads();
+  // every pair meets once in any N - 1 consecutive steps, so N - 1 steps in a
+  // row without a rotation mean convergence (same result as a quiet sweep)
+  int quiet = 0;
+  bool converged = false;
+  for (; sweeps < kJacobiMaxSweeps && !converged; ++sweeps) {
     for (int r = 0; r < N - 1; ++r) {
+      if (tid == 0) sh_active = 0;
+      __syncthreads();
       // rotations of this step
       for (int i = tid; i < P; i += kJacobiNT) {
         int p, q;
@@ -194,6 +198,11 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         }
       }
       __syncthreads();
+      quiet = sh_active ? 0 : quiet + 1;
+      if (quiet >= N - 1) {
+        converged = true;
+        break;  // uniform over the block (sh_active read after the barrier)
+      }
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;
       for (int b = tid; b < nblk; b += kJacobiNT) {
@@ -243,9 +252,6 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
       }
       __syncthreads();
     }
-    const int any = sh_active;
-    __syncthreads();
-    if (!any) break;
   }
 
   // eigenvalues with the PD guard
@@ -295,7 +301,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
     s.B[i + static_cast<long long>(ldn) * rk[j]] = sg[j] * V[i + lda * j];
   }
   if (tid == 0) {
-    const int done_sweeps = sweeps < kJacobiMaxSweeps ? sweeps + 1 : sweeps;
+    const int done_sweeps = sweeps;
     s.eig_sweeps = done_sweeps;
     s.eig_count += 1;
     s.eig_sweeps_total += done_sweeps;

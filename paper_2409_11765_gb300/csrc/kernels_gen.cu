@@ -29,6 +29,7 @@ int tiles_sample_z(int n, int lam_cap) { return ceil_div(ceil_div(n, 2) * lam_ca
 int tiles_gemm_panel(int n, int lam_cap) { return ceil_div(n, kGBM) * ceil_div(lam_cap, kGBN); }
 int tiles_colreduce(int lam_cap) { return ceil_div(lam_cap, 8); }
 int tiles_rank(int lam_cap) { return ceil_div(lam_cap, 256); }
+int tiles_rank2d(int lam_cap) { return ceil_div(lam_cap, 256) * ceil_div(lam_cap, kRankChunk); }
 int tiles_rows(int n) { return ceil_div(n, 256); }
 int tiles_recomb(int n, int mu_cap) { return ceil_div(n, 32) * ceil_div(mu_cap, 256); }
 int tiles_gemv(int n) { return ceil_div(n, 32) * ceil_div(n, 256); }
@@ -143,6 +144,7 @@ __global__ void __launch_bounds__(256) k_sample_z(Search* S, TileMap tm, DevOpti
   double z0, z1;
   normal_pair(static_cast<uint32_t>(j), static_cast<uint32_t>(k), static_cast<uint32_t>(s.gen),
               stream_word(s.index, s.restart), o.key0, o.key1, z0, z1);
+  if (j == 0) s.rank[k] = 0;  // k_rank accumulates into it
   double* col = s.Z + static_cast<long long>(ldn) * k;
   if (2 * j + 1 < n) {
     *reinterpret_cast<double2*>(col + 2 * j) = make_double2(z0, z1);
@@ -251,40 +253,50 @@ void launch_colreduce_f(Search* S, TileMap tm, cudaStream_t st) {
 
 // --------------------------------- ranking ----------------------------------
 // rank(k) = #{j : (key_j, j) < (key_k, k)} with key = f, NaN -> +inf. A
-// counting rank is stable by construction and needs no data-dependent
-// control flow; order[rank(k)] = k.
+// counting rank is stable by construction; order[rank(k)] = k. The j range is
+// split into chunks of kRankChunk handled by separate blocks that add their
+// integer counts atomically (integer sums do not depend on the order).
+// rank[] is cleared by k_sample_z (the ask/tell path also samples first).
 __device__ __forceinline__ double rank_key(double f) { return isnan(f) ? INFINITY : f; }
 
 __global__ void __launch_bounds__(256) k_rank(Search* S, TileMap tm) {
-  __shared__ double keys[256];
+  __shared__ double keys[kRankChunk];
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
   if (s.done) return;
   const int lam = s.lam;
-  if (t * 256 >= lam) return;
-  const int k = t * 256 + threadIdx.x;
+  const int nkt = ceil_div(s.lam_cap, 256);
+  const int kt = t % nkt, jc = t / nkt;
+  const int j0 = jc * kRankChunk;
+  if (kt * 256 >= lam || j0 >= lam) return;
+  const int k = kt * 256 + threadIdx.x;
   const double* f = s.f;
-  const double key = (k < lam) ? rank_key(f[k]) : 0.0;
+  const int jn = min(kRankChunk, lam - j0);
+  for (int q = threadIdx.x; q < jn; q += 256) keys[q] = rank_key(f[j0 + q]);
+  __syncthreads();
+  if (k >= lam) return;
+  const double key = rank_key(f[k]);
   int cnt = 0;
-  for (int j0 = 0; j0 < lam; j0 += 256) {
-    __syncthreads();
-    if (j0 + static_cast<int>(threadIdx.x) < lam) keys[threadIdx.x] = rank_key(f[j0 + threadIdx.x]);
-    __syncthreads();
-    const int jn = min(256, lam - j0);
-    for (int jj = 0; jj < jn; ++jj) {
-      const double kj = keys[jj];
-      cnt += (kj < key) || (kj == key && j0 + jj < k);
-    }
+  for (int jj = 0; jj < jn; ++jj) {
+    const double kj = keys[jj];
+    cnt += (kj < key) || (kj == key && j0 + jj < k);
   }
-  if (k < lam) {
-    s.rank[k] = cnt;
-    s.order[cnt] = k;
-  }
+  if (cnt) atomicAdd(&s.rank[k], cnt);
 }
 
-void launch_rank(Search* S, TileMap tm, cudaStream_t st) {
-  if (tm.total > 0) k_rank<<<tm.total, 256, 0, st>>>(S, tm);
+__global__ void __launch_bounds__(256) k_order(Search* S, TileMap tm) {
+  int t;
+  const int si = find_search(tm, t);
+  const Search& s = S[si];
+  if (s.done) return;
+  const int k = t * 256 + threadIdx.x;
+  if (k < s.lam) s.order[s.rank[k]] = k;
+}
+
+void launch_rank(Search* S, TileMap tm2d, TileMap tm, cudaStream_t st) {
+  if (tm2d.total > 0) k_rank<<<tm2d.total, 256, 0, st>>>(S, tm2d);
+  if (tm.total > 0) k_order<<<tm.total, 256, 0, st>>>(S, tm);
 }
 
 // ----------------------- recombination (two stages) --------------------------

@@ -149,8 +149,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
 
   long long rotations = 0;
   int sweeps = 0;
-  for (; sweeps < kCMaxSweeps; ++sweeps) {
-    int any_sweep = 0;
+  // every pair meets once in any N - 1 consecutive steps, so N - 1 steps in a
+  // row without a rotation mean convergence (same result as a quiet sweep)
+  int quiet = 0;
+  bool converged = false;
+  for (; sweeps < kCMaxSweeps && !converged; ++sweeps) {
     for (int step = 0; step < N - 1; ++step) {
       // (1) rotations of the local pairs
       for (int k = tid; k < nloc; k += kCNT) {
@@ -199,8 +202,12 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
         any |= ra[k];
       }
       any = __syncthreads_or(any);
+      quiet = any ? 0 : quiet + 1;
+      if (quiet >= N - 1) {
+        converged = true;
+        break;  // uniform: every CTA gathered the same rotations
+      }
       if (any) {
-        any_sweep = 1;
         // (3) A <- A J and V <- V J on the local pairs' columns
         for (int e = tid; e < nloc * n; e += kCNT) {
           const int k = e / n, r = e % n;
@@ -328,7 +335,6 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
       }
       __syncthreads();
     }
-    if (!any_sweep) break;
   }
 
   // eigenvalues into every CTA's evall
@@ -383,7 +389,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
     if (add != 0.0)
       for (int i = tid; i < n; i += kCNT) s.C[i + static_cast<long long>(ldn) * i] += add;
     if (tid == 0) {
-      const int done_sweeps = sweeps < kCMaxSweeps ? sweeps + 1 : sweeps;
+      const int done_sweeps = sweeps;
       s.eig_sweeps = done_sweeps;
       s.eig_count += 1;
       s.eig_sweeps_total += done_sweeps;
