@@ -37,13 +37,15 @@ struct cmaes_s {
   char* arena = nullptr;
   size_t arena_bytes = 0;
   int* d_off = nullptr;  // TK_COUNT x (count + 1)
+  int* d_err = nullptr;  // device status word (bit 0: a bounded wait timed out)
+  bool mixed = false;
   std::vector<int> h_off;
   cudaStream_t stream = nullptr;
   cmaes_status err = CMAES_OK;
   std::string msg;
   std::vector<int> ask_pending;
   int max_n = 0, max_n_small_jacobi = 0, max_n_cluster_jacobi = 0, max_n_global_jacobi = 0;
-  bool any_rotated = false;
+  bool any_rotated = false, any_sphere = false;
   long long launches = 0;
   // profiling
   bool profiling = false;
@@ -112,8 +114,17 @@ static cmaes_status launch_check(cmaes_t h, const char* what) {
   return CMAES_OK;
 }
 
+static cmaes_status check_device_status(cmaes_t h) {
+  int e = 0;
+  CUDA_TRY(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  if (e & 1) return set_error(h, CMAES_ETIMEOUT, "a tensor-core wait timed out on the device");
+  return CMAES_OK;
+}
+
 static cmaes_status read_search(cmaes_t h, int s, Search* out) {
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  cmaes_status r = check_device_status(h);
+  if (r != CMAES_OK) return r;
   CUDA_TRY(h, cudaMemcpy(out, h->dS + s, sizeof(Search), cudaMemcpyDeviceToHost));
   return CMAES_OK;
 }
@@ -134,21 +145,37 @@ static inline void count_launch(cmaes_t h, int phase, int total) {
 }
 
 static void enqueue_sample(cmaes_t h, int s0, int s1, cudaStream_t st) {
-  TileMap a = h->tiles(TK_SAMPLE_Z, s0, s1), b = h->tiles(TK_PANEL, s0, s1);
+  TileMap a = h->tiles(TK_SAMPLE_Z, s0, s1);
   launch_sample_z(h->dS, a, h->dopt, st);
   count_launch(h, kPhaseSample, a.total);
-  launch_gemm_sample(h->dS, b, st);
-  count_launch(h, kPhaseSample, b.total);
+  if (h->mixed) {
+    TileMap b = h->tiles(TK_TCSAMPLE, s0, s1);
+    launch_tc_sample(h->dS, b, h->opt.precision, st);
+    count_launch(h, kPhaseSample, b.total);
+  } else {
+    TileMap b = h->tiles(TK_PANEL, s0, s1);
+    launch_gemm_sample(h->dS, b, st);
+    count_launch(h, kPhaseSample, b.total);
+  }
 }
 
 static void enqueue_objective(cmaes_t h, int s0, int s1, cudaStream_t st) {
-  TileMap a = h->tiles(TK_PANEL, s0, s1), b = h->tiles(TK_COLRED, s0, s1);
+  TileMap b = h->tiles(TK_COLRED, s0, s1);
   if (h->any_rotated) {
-    launch_gemm_objective(h->dS, a, st);
-    count_launch(h, kPhaseObjective, a.total);
+    if (h->mixed) {
+      TileMap a = h->tiles(TK_TCOBJ, s0, s1);
+      launch_tc_objective(h->dS, a, h->opt.precision, st);
+      count_launch(h, kPhaseObjective, a.total);
+    } else {
+      TileMap a = h->tiles(TK_PANEL, s0, s1);
+      launch_gemm_objective(h->dS, a, st);
+      count_launch(h, kPhaseObjective, a.total);
+    }
   }
-  launch_colreduce_f(h->dS, b, st);
-  count_launch(h, kPhaseObjective, b.total);
+  if (!h->mixed || h->any_sphere) {
+    launch_colreduce_f(h->dS, b, st);
+    count_launch(h, kPhaseObjective, b.total);
+  }
 }
 
 static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
@@ -158,6 +185,10 @@ static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
   launch_rank(h->dS, r2, r, st);
   count_launch(h, kPhaseUpdate, r2.total);
   count_launch(h, kPhaseUpdate, r.total);
+  if (h->mixed) {
+    launch_reeval(h->dS, rows, st);
+    count_launch(h, kPhaseUpdate, rows.total);
+  }
   launch_recomb_partial(h->dS, rc, st);
   count_launch(h, kPhaseUpdate, rc.total);
   launch_recomb_final(h->dS, rows, st);
@@ -171,6 +202,14 @@ static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
 }
 
 static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  if (h->mixed) {
+    TileMap p = h->tiles(TK_TCCOVP, s0, s1), t = h->tiles(TK_TCSYM, s0, s1);
+    launch_tc_cov_partial(h->dS, p, h->opt.precision, st);
+    count_launch(h, kPhaseCov, p.total);
+    launch_tc_cov_reduce(h->dS, t, st);
+    count_launch(h, kPhaseCov, t.total);
+    return;
+  }
   TileMap p = h->tiles(TK_COVP, s0, s1), t = h->tiles(TK_SYM, s0, s1);
   launch_cov_partial(h->dS, p, st);
   count_launch(h, kPhaseCov, p.total);
@@ -198,6 +237,10 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   }
   launch_set_bd(h->dS, sq, st);
   count_launch(h, kPhaseEig, sq.total);
+  if (h->mixed) {
+    launch_tc_set_bdt(h->dS, sq, h->opt.precision, 0, st);
+    count_launch(h, kPhaseEig, sq.total);
+  }
 }
 
 static void enqueue_stop(cmaes_t h, int s0, int s1, cudaStream_t st) {
@@ -306,6 +349,7 @@ void cmaes_destroy(cmaes_t h) {
   if (h->arena) cudaFree(h->arena);
   if (h->dS) cudaFree(h->dS);
   if (h->d_off) cudaFree(h->d_off);
+  if (h->d_err) cudaFree(h->d_err);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -320,8 +364,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   if (count > (1 << 24)) return set_error(nullptr, CMAES_EINVAL, "at most 2^24 searches");
   cmaes_options opt;
   if (opt_in) opt = *opt_in; else cmaes_default_options(&opt);
-  if (opt.precision != CMAES_FP64)
-    return set_error(nullptr, CMAES_EUNSUPPORTED, "precision %d not available in this build", opt.precision);
+  if (opt.precision < CMAES_FP64 || opt.precision > CMAES_MIXED_BF16)
+    return set_error(nullptr, CMAES_EINVAL, "unknown precision %d", opt.precision);
   if (opt.max_restarts < 0 || opt.max_restarts > 255)
     return set_error(nullptr, CMAES_EINVAL, "max_restarts must be in [0, 255]");
   if (!(opt.box_lo < opt.box_hi)) return set_error(nullptr, CMAES_EINVAL, "box_lo must be < box_hi");
@@ -329,6 +373,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   cmaes_t h = new cmaes_s();
   h->count = count;
   h->opt = opt;
+  h->mixed = opt.precision != CMAES_FP64;
+  const int esz = tc_elem_bytes(opt.precision);
   DevOptions& d = h->dopt;
   d.max_restarts = opt.max_restarts;
   d.ipop_double = opt.ipop_double ? 1 : 0;
@@ -370,15 +416,26 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.obj = 0;
     x.sigma0 = sigma0[s];
     cov_split(n, x.mu_cap, &x.cov_kc, &x.cov_nch);
-    const size_t ldn = x.ldn, n_ = n, lc = x.lam_cap;
+    x.mixed = h->mixed ? opt.precision : 0;
+    x.kp = (n + 31) & ~31;
+    if (h->mixed) tc_cov_split(n, x.mu_cap, &x.covm_kc, &x.covm_nch);
+    const size_t ldn = x.ldn, n_ = n, lc = x.lam_cap, kp = x.kp;
     size_t b = 0;
     b += 9 * align256(ldn * 8);                       // vectors
     b += align256(static_cast<size_t>(x.mu_cap) * 8);  // w
     b += align256(static_cast<size_t>(x.hist_cap) * 8);
     b += align256(static_cast<size_t>(part_doubles(n, x.ldn, x.mu_cap)) * 8);
-    if (x.cov_nch > 1) b += align256(static_cast<size_t>(tiles_sym(n)) * x.cov_nch * 4096 * 8);
+    if (h->mixed) {
+      b += align256(static_cast<size_t>(tiles_tc_sym(n)) * x.covm_nch * 16384 * 8);
+      b += 3 * align256(n_ * kp * esz);                // BDT QTh QTl
+      b += align256(kp * lc * esz) + align256(kp * lc * 4);  // Zm Y32
+      b += align256(static_cast<size_t>(ceil_div(n, 256)) * 8);
+      b += align256(ldn * lc * 8);                     // X
+    } else {
+      if (x.cov_nch > 1) b += align256(static_cast<size_t>(tiles_sym(n)) * x.cov_nch * 4096 * 8);
+      b += 4 * align256(ldn * lc * 8);                 // Z Y X U
+    }
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
-    b += 4 * align256(ldn * lc * 8);                   // Z Y X U
     b += align256(lc * 8);                             // f
     b += 2 * align256(lc * 4);                         // order rank
     base[s] = total;
@@ -427,24 +484,42 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.w = reinterpret_cast<double*>(take(static_cast<size_t>(x.mu_cap) * 8));
     x.hist = reinterpret_cast<double*>(take(static_cast<size_t>(x.hist_cap) * 8));
     x.part = reinterpret_cast<double*>(take(static_cast<size_t>(part_doubles(x.n, x.ldn, x.mu_cap)) * 8));
-    x.covpart = x.cov_nch > 1
-                    ? reinterpret_cast<double*>(take(static_cast<size_t>(tiles_sym(x.n)) * x.cov_nch * 4096 * 8))
-                    : nullptr;
+    const size_t kp = x.kp;
+    if (h->mixed) {
+      x.covpart = reinterpret_cast<double*>(take(static_cast<size_t>(tiles_tc_sym(x.n)) * x.covm_nch * 16384 * 8));
+      x.BDT = take(n_ * kp * esz);
+      x.QTh = take(n_ * kp * esz);
+      x.QTl = take(n_ * kp * esz);
+      x.Zm = take(kp * lc * esz);
+      x.Y32 = reinterpret_cast<float*>(take(kp * lc * 4));
+      x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(ceil_div(x.n, 256)) * 8));
+    } else {
+      x.covpart = x.cov_nch > 1
+                      ? reinterpret_cast<double*>(take(static_cast<size_t>(tiles_sym(x.n)) * x.cov_nch * 4096 * 8))
+                      : nullptr;
+    }
     x.C = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.B = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.BD = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.Q = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.EA = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.ET = reinterpret_cast<double*>(take(ldn * n_ * 8));
-    x.Z = reinterpret_cast<double*>(take(ldn * lc * 8));
-    x.Y = reinterpret_cast<double*>(take(ldn * lc * 8));
-    x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
-    x.U = reinterpret_cast<double*>(take(ldn * lc * 8));
+    if (h->mixed) {
+      x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
+    } else {
+      x.Z = reinterpret_cast<double*>(take(ldn * lc * 8));
+      x.Y = reinterpret_cast<double*>(take(ldn * lc * 8));
+      x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
+      x.U = reinterpret_cast<double*>(take(ldn * lc * 8));
+    }
     x.f = reinterpret_cast<double*>(take(lc * 8));
     x.order = reinterpret_cast<int*>(take(lc * 4));
     x.rank = reinterpret_cast<int*>(take(lc * 4));
     CREATE_TRY(cudaMemcpyAsync(x.m, x0[s], n_ * 8, cudaMemcpyHostToDevice, h->stream));
   }
+  CREATE_TRY(cudaMalloc(&h->d_err, sizeof(int)));
+  CREATE_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
+  for (int s = 0; s < count; ++s) h->hs[s].err = h->d_err;
   CREATE_TRY(cudaMalloc(&h->dS, sizeof(Search) * count));
   CREATE_TRY(cudaMemcpyAsync(h->dS, h->hs.data(), sizeof(Search) * count, cudaMemcpyHostToDevice, h->stream));
   // tile prefix sums per kind
@@ -467,6 +542,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_SQUARE: t = tiles_square(x.n); break;
         case TK_COVP: t = tiles_sym(x.n) * x.cov_nch; break;
         case TK_RANK2D: t = tiles_rank2d(x.lam_cap); break;
+        case TK_TCSAMPLE: t = h->mixed ? tiles_tc_sample(x.n, x.lam_cap) : 0; break;
+        case TK_TCOBJ: t = h->mixed ? tiles_tc_objective(x.lam_cap) : 0; break;
+        case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
+        case TK_TCSYM: t = h->mixed ? tiles_tc_sym(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;
@@ -482,6 +561,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
                              h->stream));
   launch_init_params(h->dS, 0, count, h->dopt, 1, h->stream);
   h->launches += 1;
+  if (h->mixed) {  // B D = I in the tensor-core format
+    launch_tc_set_bdt(h->dS, h->tiles(TK_SQUARE, 0, count), opt.precision, 1, h->stream);
+    h->launches += 1;
+  }
   CREATE_TRY(cudaGetLastError());
   CREATE_TRY(cudaStreamSynchronize(h->stream));
   h->ask_pending.assign(count, 0);
@@ -515,9 +598,19 @@ cmaes_status cmaes_set_problem(cmaes_t h, int s, int kind, const double* Q, cons
   if (lambda_diag) CUDA_TRY(h, cudaMemcpy(x.lamdiag, lambda_diag, n * 8, cudaMemcpyHostToDevice));
   x.obj = kind;
   CUDA_TRY(h, cudaMemcpy(&h->dS[s].obj, &x.obj, sizeof(int), cudaMemcpyHostToDevice));
+  if (h->mixed && kind != CMAES_OBJ_SPHERE) {
+    launch_tc_prepare_q(h->dS, s, h->opt.precision, h->stream);
+    h->launches += 1;
+    cmaes_status r = launch_check(h, "prepare_q");
+    if (r != CMAES_OK) return r;
+    CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  }
   h->any_rotated = false;
-  for (const Search& y : h->hs)
+  h->any_sphere = false;
+  for (const Search& y : h->hs) {
     if (y.obj == CMAES_OBJ_ELLIPSOID || y.obj == CMAES_OBJ_RASTRIGIN) h->any_rotated = true;
+    if (y.obj == CMAES_OBJ_SPHERE) h->any_sphere = true;
+  }
   return CMAES_OK;
 }
 
@@ -554,7 +647,7 @@ cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream) {
 cmaes_status cmaes_sync(cmaes_t h) {
   CHECK_HANDLE(h);
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
-  return CMAES_OK;
+  return check_device_status(h);
 }
 
 cmaes_status cmaes_ask_device(cmaes_t h, int s, const double** X_dev, int* ld) {
@@ -739,6 +832,10 @@ cmaes_status cmaes_set_state(cmaes_t h, int s, const cmaes_state* st) {
   TileMap sq = h->tiles(TK_SQUARE, s, s + 1);
   launch_set_bd_force(h->dS, sq, h->stream);
   h->launches += 1;
+  if (h->mixed) {
+    launch_tc_set_bdt(h->dS, sq, h->opt.precision, 1, h->stream);
+    h->launches += 1;
+  }
   if ((r = launch_check(h, "set_state")) != CMAES_OK) return r;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   return CMAES_OK;

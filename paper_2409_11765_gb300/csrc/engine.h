@@ -51,6 +51,15 @@ struct Search {
   int done, flags, eig_due, eig_sweeps, pad_;
   // eigensolver work counters (decompositions, sweeps, rotations applied)
   long long eig_count, eig_sweeps_total, eig_rotations;
+  // mixed precision (precision != FP64): tensor-core operands, K padded to kp
+  int mixed, kp, covm_kc, covm_nch;
+  void *BDT;          // n x kp, row i = (B diag(D))(i, :), input format (TF32 / BF16)
+  void *QTh, *QTl;    // n x kp, row i = Q(i, :), hi and lo parts
+  void *Zm;           // kp x lam_cap, z in input format (candidate columns)
+  float *Y32;         // kp x lam_cap, y = B D z from the FP32 accumulators
+  double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation
+  double fbest64;     // FP64 value of this generation's best point
+  int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
 // Flattened tiles of one kernel over a contiguous range of searches:
@@ -79,7 +88,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -113,6 +122,20 @@ void launch_set_bd(Search* S, TileMap tm, cudaStream_t st);
 void launch_set_bd_force(Search* S, TileMap tm, cudaStream_t st);
 int jacobi_smem_max_n();
 int jacobi_smem_bytes(int n, bool smem_mats);
+
+// mixed-precision path (kernels_mixed.cu)
+int tiles_tc_sample(int n, int lam_cap);
+int tiles_tc_objective(int lam_cap);
+int tiles_tc_sym(int n);
+void tc_cov_split(int n, int mu_cap, int* kc, int* nch);
+int tc_elem_bytes(int precision);
+void launch_tc_prepare_q(Search* S, int s, int precision, cudaStream_t st);
+void launch_tc_set_bdt(Search* S, TileMap tm, int precision, int force, cudaStream_t st);
+void launch_tc_sample(Search* S, TileMap tm, int precision, cudaStream_t st);
+void launch_tc_objective(Search* S, TileMap tm, int precision, cudaStream_t st);
+void launch_tc_cov_partial(Search* S, TileMap tm, int precision, cudaStream_t st);
+void launch_tc_cov_reduce(Search* S, TileMap tm, cudaStream_t st);
+void launch_reeval(Search* S, TileMap tm, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);

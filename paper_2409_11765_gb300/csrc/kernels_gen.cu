@@ -20,7 +20,9 @@
 // current lambda exit at once, which keeps launch shapes fixed across the
 // lambda changes of IPOP restarts.
 #include <cmath>
+#include <cuda_bf16.h>
 #include "device_common.cuh"
+#include "tc_common.cuh"
 
 namespace cmaes_gb300 {
 
@@ -98,6 +100,15 @@ __device__ void reset_descent(Search& s) {
     s.B[e] = v;
     s.BD[e] = v;
   }
+  if (s.mixed) {  // tensor-core copy of B D: identity as well
+    const int kp = s.kp;
+    for (long long e = threadIdx.x; e < static_cast<long long>(n) * kp; e += NT) {
+      const int i = static_cast<int>(e / kp), k = static_cast<int>(e % kp);
+      const float v = (i == k) ? 1.0f : 0.0f;
+      if (s.mixed == 2) static_cast<__nv_bfloat16*>(s.BDT)[e] = __float2bfloat16_rn(v);
+      else static_cast<float*>(s.BDT)[e] = v;
+    }
+  }
   if (threadIdx.x == 0) {
     s.sigma = s.sigma0;
     s.gen = 0;
@@ -145,6 +156,20 @@ __global__ void __launch_bounds__(256) k_sample_z(Search* S, TileMap tm, DevOpti
   normal_pair(static_cast<uint32_t>(j), static_cast<uint32_t>(k), static_cast<uint32_t>(s.gen),
               stream_word(s.index, s.restart), o.key0, o.key1, z0, z1);
   if (j == 0) s.rank[k] = 0;  // k_rank accumulates into it
+  if (s.mixed) {
+    // z in the tensor-core input format; the recombination reads the same values
+    const long long e0 = static_cast<long long>(s.kp) * k + 2 * j;
+    if (s.mixed == 2) {
+      __nv_bfloat16* zc = static_cast<__nv_bfloat16*>(s.Zm);
+      zc[e0] = __float2bfloat16_rn(static_cast<float>(z0));
+      if (2 * j + 1 < n) zc[e0 + 1] = __float2bfloat16_rn(static_cast<float>(z1));
+    } else {
+      float* zc = static_cast<float*>(s.Zm);
+      zc[e0] = to_tf32(static_cast<float>(z0));
+      if (2 * j + 1 < n) zc[e0 + 1] = to_tf32(static_cast<float>(z1));
+    }
+    return;
+  }
   double* col = s.Z + static_cast<long long>(ldn) * k;
   if (2 * j + 1 < n) {
     *reinterpret_cast<double2*>(col + 2 * j) = make_double2(z0, z1);
@@ -224,7 +249,7 @@ __global__ void __launch_bounds__(256) k_colreduce_f(Search* S, TileMap tm) {
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
-  if (s.done) return;
+  if (s.done || (s.mixed && s.obj != 3)) return;
   const int n = s.n, ldn = s.ldn, lam = s.lam;
   const int k = t * 8 + (threadIdx.x >> 5), lane = threadIdx.x & 31;
   if (k >= lam) return;
@@ -318,12 +343,21 @@ __global__ void __launch_bounds__(256) k_recomb_partial(Search* S, TileMap tm) {
   const int i = rt * 32 + lane;
   const int r1 = min(mu, r0 + 256);
   double ay = 0.0, az = 0.0;
-  if (i < n) {
+  if (i < n && !s.mixed) {
     for (int r = r0 + w; r < r1; r += 8) {
       const long long col = static_cast<long long>(ldn) * s.order[r];
       const double wr = s.w[r];
       ay = fma(wr, s.Y[col + i], ay);
       az = fma(wr, s.Z[col + i], az);
+    }
+  } else if (i < n) {
+    for (int r = r0 + w; r < r1; r += 8) {
+      const long long col = static_cast<long long>(s.kp) * s.order[r];
+      const double wr = s.w[r];
+      const double z = (s.mixed == 2) ? static_cast<double>(__bfloat162float(static_cast<const __nv_bfloat16*>(s.Zm)[col + i]))
+                                      : static_cast<double>(static_cast<const float*>(s.Zm)[col + i]);
+      ay = fma(wr, static_cast<double>(s.Y32[col + i]), ay);
+      az = fma(wr, z, az);
     }
   }
   shy[w][lane] = ay;
@@ -435,7 +469,13 @@ __global__ void __launch_bounds__(256) k_finalize(Search* S, int s0) {
     s.m[i] = s.m[i] + sigma * y;
   }
   const int i0 = s.order[0];
-  const double f0 = s.f[i0];
+  double f0 = s.f[i0];
+  if (s.mixed && s.obj != 0) {
+    // the value that decides the best point and the history is the FP64 one
+    double acc = 0.0;
+    for (int t = 0; t < ceil_div(n, 256); ++t) acc += s.fpart[t];
+    f0 = (s.obj == 2) ? 10.0 * n + acc : acc;
+  }
   const bool better = f0 < s.best_f;
   if (better) {
     const double* x = s.X + static_cast<long long>(s.ldn) * i0;
