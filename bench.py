@@ -43,7 +43,9 @@ def parse_args():
     ap.add_argument("--steps", type=int, default=200)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
-    ap.add_argument("--precision", choices=["fp64"], default="fp64")
+    ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="tf32",
+                    help="headline path; the other two are measured beside it")
+    ap.add_argument("--headline-only", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=50)
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -67,7 +69,10 @@ def workload_config(wl, precision):
             "candidates_per_step": wl.candidates_per_generation,
             "objective": "rotated Rastrigin (seeded Haar Q, x* ~ U[-4,4]^n)",
             "layout": "K-Distributed: levels lambda=17*2^k, k=0..9, one batch",
-            "precision": precision, "eig": "FP64 warm-started Jacobi, every generation (lazy rule gives 1)",
+            "precision": precision,
+            "gemms": {"fp64": "FP64 CUDA cores", "tf32": "tcgen05 kind::tf32 (objective, rank-mu: 3-term split)",
+                      "bf16": "tcgen05 kind::f16 bf16 (objective, rank-mu: 3-term split)"}[precision],
+            "eig": "FP64 warm-started Jacobi, every generation (lazy rule gives 1)",
             "l2": "256 MiB write between timed generations", "seed": 20240918}
 
 
@@ -195,6 +200,115 @@ def eig_flops(n, rotations, decompositions):
     return 4.0 * n ** 3 * decompositions + 12.0 * n * rotations
 
 
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
+
+
+def phase_flops(wl, prec_name, eig):
+    """Algorithmic work per step of each phase (flops), for the roofline."""
+    n = wl.searches[0].n
+    count = len(wl.searches)
+    lam_sum = wl.candidates_per_generation
+    mu_sum = sum(s.lam // 2 for s in wl.searches)
+    split = 1 if prec_name == "fp64" else 3   # split operands: three products
+    return {
+        "sample": 2.0 * lam_sum * n * n,
+        "objective": 2.0 * lam_sum * n * n * split,
+        "cov": (1.0 * mu_sum * n * (n + 1)) * split + 3.0 * count * n * n,
+        "eig": eig,
+        "update": 2.0 * count * n * n + 4.0 * mu_sum * n,
+        "stop": 0.0,
+    }
+
+
+def measure(args, prec_name, world, rank, dist, want_clocks):
+    import torch
+    import paper_2409_11765_gb300 as eng
+    wl = workload()
+    count = len(wl.searches)
+    opt = eng.cmaes_default_options(precision=PREC[prec_name], f_target=wl.f_target,
+                                    box_lo=wl.box_lo, box_hi=wl.box_hi, max_restarts=255,
+                                    ipop_double=0)
+    ns = [s.n for s in wl.searches]
+    h = eng.cmaes_create_batch(ns, [s.lam for s in wl.searches], [s.x0 for s in wl.searches],
+                               [s.sigma0 for s in wl.searches], 20240918 + 7919 * rank, opt)
+    try:
+        for i, s in enumerate(wl.searches):
+            p = s.problem
+            eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
+        # a dedicated stream: the engine launches on it and the CUDA events
+        # that time the steps are recorded on it
+        stream = torch.cuda.Stream()
+        torch.cuda.set_stream(stream)
+        sptr = stream.cuda_stream
+        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+        for _ in range(args.warmup):
+            eng.cmaes_step_batch(h, 1, sptr)
+        torch.cuda.synchronize()
+        eig0 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
+        eng.cmaes_phase_times(h, reset=True)
+        eng.cmaes_set_profiling(h, True)
+        launches0 = eng.cmaes_kernel_launches(h)
+        starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
+        sampler = None
+        if want_clocks:
+            vis = os.environ.get("CUDA_VISIBLE_DEVICES")
+            local = int(os.environ.get("LOCAL_RANK", "0"))
+            gpu_index = vis.split(",")[local] if vis else str(local)
+            sampler = ClockSampler(gpu_index)
+            time.sleep(0.3)
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            starts[k].record(stream)
+            eng.cmaes_step_batch(h, 1, sptr)
+            ends[k].record(stream)
+        torch.cuda.synchronize()
+        if dist is not None:
+            dist.barrier()
+        clocks = sampler.stop() if sampler else None
+        launches = eng.cmaes_kernel_launches(h) - launches0
+        eng.cmaes_set_profiling(h, False)
+        phase_ms, _ = eng.cmaes_phase_times(h, reset=True)
+        total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
+        if dist is not None:
+            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            total_ms = float(t.item())
+        eig1 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
+        dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
+        rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
+        swp = sum(b["sweeps"] - a["sweeps"] for a, b in zip(eig0, eig1))
+        torch.cuda.set_stream(torch.cuda.default_stream())
+        # e2e through the public API: one generation and a host read of every
+        # search's best point and value, synchronised each step
+        e2e_t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            eng.cmaes_step_batch(h, 1)
+            for i in range(count):
+                eng.cmaes_best(h, i, ns[i])
+        e2e_el = time.perf_counter() - e2e_t0
+    finally:
+        eng.cmaes_destroy(h)
+    cand = wl.candidates_per_generation
+    n = ns[0]
+    flops = phase_flops(wl, prec_name, eig_flops(n, rot, dec) / args.steps)
+    return {
+        "value": cand * args.steps * world / (total_ms / 1e3),
+        "ms_per_step": total_ms / args.steps,
+        "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
+        "phase_flops_per_step": flops,
+        "gpu_launches": int(launches),
+        "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot},
+        "e2e": {"value": cand * args.e2e_steps * world / e2e_el, "unit": UNIT,
+                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": sum(8 * m + 8 for m in ns)},
+        "clocks": clocks,
+    }
+
+
 def run_engine(args):
     import torch
     rank, local_rank, world = dist_env()
@@ -203,7 +317,6 @@ def run_engine(args):
     if world > 1:
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local_rank))
-
     import paper_2409_11765_gb300 as eng
     from paper_2409_11765_gb300 import _build
     if rank == 0 or world == 1:
@@ -211,115 +324,53 @@ def run_engine(args):
     if dist is not None:
         dist.barrier()
 
-    wl = workload()
-    count = len(wl.searches)
-    opt = eng.cmaes_default_options(f_target=wl.f_target, box_lo=wl.box_lo, box_hi=wl.box_hi,
-                                    max_restarts=255, ipop_double=0)
-    ns = [s.n for s in wl.searches]
-    h = eng.cmaes_create_batch(ns, [s.lam for s in wl.searches], [s.x0 for s in wl.searches],
-                               [s.sigma0 for s in wl.searches], 20240918 + 7919 * rank, opt)
-    for i, s in enumerate(wl.searches):
-        p = s.problem
-        eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
+    head = args.precision
+    runs = {head: measure(args, head, world, rank, dist, want_clocks=True)}
+    for other in ("fp64", "tf32", "bf16"):
+        if other != head and not args.headline_only:
+            runs[other] = measure(args, other, world, rank, dist, want_clocks=False)
+    r = runs[head]
 
-    # a dedicated stream: the engine launches on it and the CUDA events that
-    # time the steps are recorded on it
-    stream = torch.cuda.Stream()
-    torch.cuda.set_stream(stream)
-    sptr = stream.cuda_stream
-    assert sptr != 0
-    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
-    for _ in range(args.warmup):
-        eng.cmaes_step_batch(h, 1, sptr)
-    torch.cuda.synchronize()
-
-    eig0 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
-    eng.cmaes_phase_times(h, reset=True)
-    eng.cmaes_set_profiling(h, True)
-    launches0 = eng.cmaes_kernel_launches(h)
-    starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
-    gpu_index = os.environ.get("CUDA_VISIBLE_DEVICES", str(local_rank)).split(",")[local_rank] \
-        if os.environ.get("CUDA_VISIBLE_DEVICES") else str(local_rank)
-    sampler = ClockSampler(gpu_index)
-    time.sleep(0.3)
-    if dist is not None:
-        dist.barrier()
-    torch.cuda.synchronize()
-    wall0 = time.perf_counter()
-    for k in range(args.steps):
-        flush.fill_(k & 255)
-        starts[k].record(stream)
-        eng.cmaes_step_batch(h, 1, sptr)
-        ends[k].record(stream)
-    torch.cuda.synchronize()
-    if dist is not None:
-        dist.barrier()
-    wall = time.perf_counter() - wall0
-    clocks = sampler.stop()
-    launches = eng.cmaes_kernel_launches(h) - launches0
-    eng.cmaes_set_profiling(h, False)
-    phase_ms, phase_launch = eng.cmaes_phase_times(h, reset=True)
-    total_ms = sum(s.elapsed_time(e) for s, e in zip(starts, ends))
-    if dist is not None:
-        t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-    cand_step = wl.candidates_per_generation
-    value = cand_step * args.steps * world / (total_ms / 1e3)
-
-    eig1 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
-    dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
-    rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
-    swp = sum(b["sweeps"] - a["sweeps"] for a, b in zip(eig0, eig1))
-
-    # e2e through the public API: one generation + a host read of every
-    # search's best point and value, synchronised each step
-    import numpy as np
-    e2e_t0 = time.perf_counter()
-    for _ in range(args.e2e_steps):
-        eng.cmaes_step_batch(h, 1)
-        for i in range(count):
-            eng.cmaes_best(h, i, ns[i])
-    e2e_el = time.perf_counter() - e2e_t0
-    e2e_value = cand_step * args.e2e_steps * world / e2e_el
-    d2h = sum(8 * n + 8 for n in ns)
-
-    # roofline of the dominant phase
+    # roofline of the dominant phase of the headline run
     fp64_peak = eng.probe_fma_tflops(64)
-    dom = max(phase_ms, key=phase_ms.get)
-    n = ns[0]
-    lam_sum = cand_step
-    mu_sum = sum(s.lam // 2 for s in wl.searches)
-    phase_flops = {
-        "sample": 2.0 * lam_sum * n * n,
-        "objective": 2.0 * lam_sum * n * n,
-        "cov": 1.0 * mu_sum * n * (n + 1) + 3.0 * count * n * n,
-        "eig": eig_flops(n, rot, dec) / args.steps,
-        "update": 2.0 * count * n * n + 4.0 * mu_sum * n,
-        "stop": 0.0,
-    }
-    dom_ms = phase_ms[dom] / args.steps
-    achieved = phase_flops[dom] / (dom_ms * 1e-3) / 1e12
-    roofline = {"bound": "alu", "achieved": achieved, "peak": fp64_peak, "unit": "TFLOP/s",
-                "frac": achieved / fp64_peak, "traffic": None,
-                "kernel": dom, "peak_source": "FP64 DFMA probe measured live on this GPU",
-                "algorithmic_flops_per_step": phase_flops[dom]}
-    eng.cmaes_destroy(h)
-
+    import json as _json
+    peaks = {}
+    try:
+        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except (OSError, ValueError):
+        pass
+    dom = max(r["phases_ms_per_step"], key=r["phases_ms_per_step"].get)
+    dom_ms = r["phases_ms_per_step"][dom]
+    achieved = r["phase_flops_per_step"][dom] / (dom_ms * 1e-3) / 1e12
+    if dom in ("eig", "update", "stop") or head == "fp64":
+        bound, peak, src = "alu", fp64_peak, "FP64 DFMA probe measured live on this GPU"
+    else:
+        bf16 = peaks.get("bf16_tflops", 1908.7)
+        peak = bf16 * (0.5 if head == "tf32" else 1.0)
+        bound, src = "tensor", ("MEASURED_PEAKS.json bf16 x nominal tf32/bf16 ratio 0.5"
+                                if head == "tf32" else "MEASURED_PEAKS.json bf16")
+    roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": src,
+                "algorithmic_flops_per_step": r["phase_flops_per_step"][dom]}
     if rank != 0:
+        if dist is not None:
+            dist.destroy_process_group()
         return
-    line = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": total_ms / args.steps, "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": workload_config(wl, args.precision), "roofline": roofline,
-            "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": 0,
-                    "d2h_bytes_per_step": d2h},
-            "gpu_launches": int(launches), "clocks": clocks,
-            "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-            "eig_ms_per_step": phase_ms["eig"] / args.steps,
-            "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot},
-            "wall_s_timed_loop": wall}
+    wl = workload()
+    line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": DTYPE[head], "data": "synthetic", "config": workload_config(wl, head),
+            "roofline": roofline, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+            "clocks": r["clocks"], "phases_ms_per_step": r["phases_ms_per_step"],
+            "eig_ms_per_step": r["phases_ms_per_step"]["eig"], "eig_work": r["eig_work"]}
+    for other, o in runs.items():
+        if other != head:
+            line[other + "_path"] = {"value": o["value"], "ms_per_step": o["ms_per_step"],
+                                     "phases_ms_per_step": o["phases_ms_per_step"],
+                                     "eig_work": o["eig_work"]}
+    if "fp64_path" in line:
+        line["mixed_over_fp64"] = r["value"] / line["fp64_path"]["value"]
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line), flush=True)
