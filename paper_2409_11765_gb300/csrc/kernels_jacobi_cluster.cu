@@ -5,22 +5,23 @@
 // output as the single-CTA variant; only the data placement differs:
 //   * Tournament slots. Pair i of a round-robin step is (T[i], Bt[i]); CTA c
 //     owns slots [c spc, (c+1) spc) and keeps the full columns of A and of the
-//     eigenvector accumulator V for the players sitting in its slots.
-//   * Each step: every CTA computes the rotations of its own pairs (all data
-//     local), publishes them, and after a cluster barrier reads everybody's
-//     rotations through distributed shared memory. A <- A J (column mixing)
-//     and V <- V J touch only the owner's two columns; A <- J^T A (row mixing)
-//     touches rows p_i, q_i of every column, so each CTA applies all
-//     rotations to its own columns. The 2 x 2 diagonal block of every rotated
-//     pair is then set exactly (a_pq = 0, a_pp -= t a_pq, a_qq += t a_pq).
+//     eigenvector accumulator V for the players sitting in its slots. One warp
+//     serves one slot.
+//   * Each step: every warp computes its pair's rotation from its own two
+//     columns and writes it into the rotation table of every CTA of the
+//     cluster (distributed shared memory). After a cluster barrier each warp
+//     applies A <- A J and V <- V J to its two columns (column mixing), then
+//     A <- J^T A to the rows p_i, q_i of its two columns for every rotated pair
+//     (row mixing), then sets its pair's 2 x 2 diagonal block exactly
+//     (a_pq = 0, a_pp - t a_pq, a_qq + t a_pq). All of this is warp-local.
 //   * Between steps the players move one place along the ring
 //     T[1] -> ... -> T[P-1] -> Bt[P-1] -> ... -> Bt[0] -> T[1] (T[0] fixed),
-//     which is the circle method: every pair meets once per N - 1 steps. Moves
-//     inside a CTA only relabel buffers; a move across CTAs copies the column
-//     (A and V parts) into a landing buffer of the neighbour, followed by a
-//     second cluster barrier.
-// Control flow is uniform over the cluster: every CTA reads the same search
-// flags and the same gathered rotations, so all reach the same barriers.
+//     the circle method: every pair meets once in any N - 1 steps. A column
+//     leaving the CTA is written into a landing buffer of the neighbour; a
+//     second cluster barrier separates those writes from their use.
+// The two cluster barriers are the only synchronisation of a step. Control
+// flow is uniform over the cluster: every CTA reads the same search flags and
+// the same rotation table, so all reach the same barriers.
 #include <cmath>
 #include <cooperative_groups.h>
 #include "device_common.cuh"
@@ -30,7 +31,6 @@ namespace cg = cooperative_groups;
 namespace cmaes_gb300 {
 
 constexpr int kCS = 8;            // CTAs per cluster (portable size)
-constexpr int kCNT = 256;         // threads per CTA
 constexpr int kClusterMaxN = 256;
 constexpr double kCTol = 1e-14;   // same relative threshold as the single-CTA variant
 constexpr int kCMaxSweeps = 40;
@@ -39,12 +39,10 @@ constexpr double kCPdFloor = 1e-16;
 namespace {
 
 struct CLayout {
-  int stride, nbuf, spc, P, N;
+  int stride, nbuf, spc, P, N, threads;
   size_t bytes;
-  // double arrays
-  size_t colA, colV, ac, as, lc, ls, lt, lapp, laqq, lapq, evall;
-  // int arrays
-  size_t ids, tb, bb, ap, aq, aa, lp, lq, la, nmap;
+  size_t colA, colV, rc, rs, evall;     // double arrays
+  size_t ids, rp, rq, ra, map;          // int arrays
 };
 
 __host__ __device__ inline CLayout make_layout(int max_n) {
@@ -54,29 +52,19 @@ __host__ __device__ inline CLayout make_layout(int max_n) {
   L.spc = (L.P + kCS - 1) / kCS;
   L.nbuf = 2 * L.spc + 2;
   L.stride = max_n + 1;
+  L.threads = 32 * (L.spc > 2 ? L.spc : 2);
   size_t d = 0;
   L.colA = d; d += static_cast<size_t>(L.nbuf) * L.stride;
   L.colV = d; d += static_cast<size_t>(L.nbuf) * L.stride;
-  L.ac = d; d += L.P;
-  L.as = d; d += L.P;
-  L.lc = d; d += L.spc;
-  L.ls = d; d += L.spc;
-  L.lt = d; d += L.spc;
-  L.lapp = d; d += L.spc;
-  L.laqq = d; d += L.spc;
-  L.lapq = d; d += L.spc;
+  L.rc = d; d += L.P;
+  L.rs = d; d += L.P;
   L.evall = d; d += L.N;
   size_t i = 0;
   L.ids = i; i += L.nbuf;
-  L.tb = i; i += L.spc;
-  L.bb = i; i += L.spc;
-  L.ap = i; i += L.P;
-  L.aq = i; i += L.P;
-  L.aa = i; i += L.P;
-  L.lp = i; i += L.spc;
-  L.lq = i; i += L.spc;
-  L.la = i; i += L.spc;
-  L.nmap = i; i += 2 * L.spc + 8;  // new slot map and copy plan
+  L.rp = i; i += L.P;
+  L.rq = i; i += L.P;
+  L.ra = i; i += L.P;
+  L.map = i; i += 4 * L.spc;  // two parities x (top, bottom) buffer of each local slot
   L.bytes = d * 8 + i * 4 + 16;
   return L;
 }
@@ -86,7 +74,7 @@ __host__ __device__ inline CLayout make_layout(int max_n) {
 size_t jacobi_cluster_smem_bytes(int max_n) { return make_layout(max_n).bytes; }
 int jacobi_cluster_max_n() { return kClusterMaxN; }
 
-__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
+__global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
     k_jacobi_cluster(Search* S, int s0, int lo_n, int hi_n, int layout_n) {
   extern __shared__ double dsm[];
   __shared__ double shr[32];
@@ -99,26 +87,15 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
   const CLayout L = make_layout(layout_n);
   double* colA = dsm + L.colA;
   double* colV = dsm + L.colV;
-  double* ac = dsm + L.ac;
-  double* as = dsm + L.as;
-  double* lc = dsm + L.lc;
-  double* ls = dsm + L.ls;
-  double* lt = dsm + L.lt;
-  double* lapp = dsm + L.lapp;
-  double* laqq = dsm + L.laqq;
-  double* lapq = dsm + L.lapq;
+  double* rc = dsm + L.rc;
+  double* rs = dsm + L.rs;
   double* evall = dsm + L.evall;
   int* ibase = reinterpret_cast<int*>(dsm + (L.evall + L.N));
   int* ids = ibase + L.ids;
-  int* tb = ibase + L.tb;
-  int* bb = ibase + L.bb;
-  int* ap = ibase + L.ap;
-  int* aq = ibase + L.aq;
-  int* aa = ibase + L.aa;
-  int* lp = ibase + L.lp;
-  int* lq = ibase + L.lq;
-  int* la = ibase + L.la;
-  int* nmap = ibase + L.nmap;  // [0, spc): new tb, [spc, 2spc): new bb, then copy plan
+  int* rp = ibase + L.rp;
+  int* rq = ibase + L.rq;
+  int* ra = ibase + L.ra;
+  int* map = ibase + L.map;  // map[par * 2 spc + 2 k] = top buffer, +1 = bottom buffer
 
   const int n = s.n, ldn = s.ldn;
   const int N = n + (n & 1), P = N / 2;
@@ -126,16 +103,18 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
   const int g0 = min(P, crank * spc), g1 = min(P, g0 + spc), nloc = g1 - g0;
   const int st = L.stride;
   const int IN_TOP = 2 * spc, IN_BOT = 2 * spc + 1;
-  const int tid = threadIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const bool mine = warp < nloc;  // this warp serves local slot `warp`
+  const int k = warp;
 
-  // initial seating T[i] = 2i, Bt[i] = 2i + 1; buffer b of this CTA holds
+  // initial seating T[i] = 2i, Bt[i] = 2i + 1: buffer b of this CTA holds
   // player 2 g0 + b; A symmetrised from EA = B^T C B, V = B
-  for (int k = tid; k < nloc; k += kCNT) {
-    tb[k] = 2 * k;
-    bb[k] = 2 * k + 1;
+  for (int b = tid; b < 2 * nloc; b += blockDim.x) ids[b] = 2 * g0 + b;
+  for (int i = tid; i < nloc; i += blockDim.x) {
+    map[2 * i] = 2 * i;
+    map[2 * i + 1] = 2 * i + 1;
   }
-  for (int b = tid; b < 2 * nloc; b += kCNT) ids[b] = 2 * g0 + b;
-  for (int e = tid; e < 2 * nloc * n; e += kCNT) {
+  for (int e = tid; e < 2 * nloc * n; e += blockDim.x) {
     const int b = e / n, r = e % n, id = 2 * g0 + b;
     double a = 0.0, v = 0.0;
     if (id < n) {
@@ -148,23 +127,23 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
   __syncthreads();
 
   long long rotations = 0;
-  int sweeps = 0;
-  // every pair meets once in any N - 1 consecutive steps, so N - 1 steps in a
-  // row without a rotation mean convergence (same result as a quiet sweep)
-  int quiet = 0;
+  int sweeps = 0, quiet = 0, par = 0;
   bool converged = false;
   for (; sweeps < kCMaxSweeps && !converged; ++sweeps) {
     for (int step = 0; step < N - 1; ++step) {
-      // (1) rotations of the local pairs
-      for (int k = tid; k < nloc; k += kCNT) {
-        const int bp = tb[k], bq = bb[k];
-        const int p = ids[bp], q = ids[bq];
-        double c = 1.0, sn = 0.0, tn = 0.0, app = 0.0, aqq = 0.0, apq = 0.0;
-        int act = 0;
+      const int* mp = map + par * 2 * spc;
+      int bt = 0, bb = 0;
+      double c = 1.0, sn = 0.0, tn = 0.0, app = 0.0, aqq = 0.0, apq = 0.0;
+      int p = 0, q = 0, act = 0;
+      if (mine) {
+        bt = mp[2 * k];
+        bb = mp[2 * k + 1];
+        p = ids[bt];
+        q = ids[bb];
         if (p < n && q < n) {
-          app = colA[bp * st + p];
-          aqq = colA[bq * st + q];
-          apq = colA[bq * st + p];
+          app = colA[bt * st + p];
+          aqq = colA[bb * st + q];
+          apq = colA[bb * st + p];
           if (apq != 0.0 && fabs(apq) > kCTol * sqrt(fabs(app * aqq))) {
             const double theta = (aqq - app) / (2.0 * apq);
             const double at = fabs(theta);
@@ -174,191 +153,172 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
             act = 1;
           }
         }
-        lc[k] = c;
-        ls[k] = sn;
-        lt[k] = tn;
-        lapp[k] = app;
-        laqq[k] = aqq;
-        lapq[k] = apq;
-        lp[k] = p;
-        lq[k] = q;
-        la[k] = act;
+        // publish the rotation in every CTA's table (lanes 0..7 write one CTA each)
+        if (lane < kCS) {
+          const int gi = g0 + k;
+          cl.map_shared_rank(rc, lane)[gi] = c;
+          cl.map_shared_rank(rs, lane)[gi] = sn;
+          cl.map_shared_rank(rp, lane)[gi] = p;
+          cl.map_shared_rank(rq, lane)[gi] = q;
+          cl.map_shared_rank(ra, lane)[gi] = act;
+        }
       }
-      cl.sync();  // rotations published
-      // (2) gather every pair's rotation
+      cl.sync();  // rotation table complete everywhere
       int any = 0;
-      for (int i = tid; i < P; i += kCNT) {
-        const int owner = i / spc, k = i - owner * spc;
-        const double* rc = cl.map_shared_rank(lc, owner);
-        const double* rs = cl.map_shared_rank(ls, owner);
-        const int* rp = cl.map_shared_rank(lp, owner);
-        const int* rq = cl.map_shared_rank(lq, owner);
-        const int* ra = cl.map_shared_rank(la, owner);
-        ac[i] = rc[k];
-        as[i] = rs[k];
-        ap[i] = rp[k];
-        aq[i] = rq[k];
-        aa[i] = ra[k];
-        any |= ra[k];
+      for (int i = lane; i < P; i += 32) any |= ra[i];
+      any = __any_sync(0xffffffffu, any);
+      if (tid == 0 && crank == 0) {
+        int cnt = 0;
+        for (int i = 0; i < P; ++i) cnt += ra[i];
+        rotations += cnt;
       }
-      any = __syncthreads_or(any);
       quiet = any ? 0 : quiet + 1;
       if (quiet >= N - 1) {
         converged = true;
-        break;  // uniform: every CTA gathered the same rotations
+        break;  // uniform: every warp of the cluster saw the same table
       }
-      if (any) {
-        // (3) A <- A J and V <- V J on the local pairs' columns
-        for (int e = tid; e < nloc * n; e += kCNT) {
-          const int k = e / n, r = e % n;
-          if (!la[k]) continue;
-          const double c = lc[k], sn = ls[k];
-          double* Ap = colA + tb[k] * st;
-          double* Aq = colA + bb[k] * st;
-          const double x = Ap[r], y = Aq[r];
-          Ap[r] = c * x - sn * y;
-          Aq[r] = sn * x + c * y;
-          double* Vp = colV + tb[k] * st;
-          double* Vq = colV + bb[k] * st;
-          const double v = Vp[r], w = Vq[r];
-          Vp[r] = c * v - sn * w;
-          Vq[r] = sn * v + c * w;
+      if (mine && any) {
+        double* At = colA + bt * st;
+        double* Ab = colA + bb * st;
+        if (act) {  // A <- A J and V <- V J on the pair's columns
+          double* Vt = colV + bt * st;
+          double* Vb = colV + bb * st;
+          for (int r = lane; r < n; r += 32) {
+            const double x = At[r], y = Ab[r];
+            At[r] = c * x - sn * y;
+            Ab[r] = sn * x + c * y;
+            const double v = Vt[r], w = Vb[r];
+            Vt[r] = c * v - sn * w;
+            Vb[r] = sn * v + c * w;
+          }
+          __syncwarp();
         }
-        __syncthreads();
-        // (4) A <- J^T A: rows p_i, q_i of every local column
-        for (int e = tid; e < 2 * nloc * P; e += kCNT) {
-          const int lb = e / P, i = e - lb * P;
-          if (!aa[i]) continue;
-          const int buf = lb < nloc ? tb[lb] : bb[lb - nloc];
-          double* col = colA + buf * st;
-          const int p = ap[i], q = aq[i];
-          const double c = ac[i], sn = as[i];
-          const double x = col[p], y = col[q];
-          col[p] = c * x - sn * y;
-          col[q] = sn * x + c * y;
+        // A <- J^T A: rows p_i, q_i of both columns, every rotated pair
+        for (int i = lane; i < P; i += 32) {
+          if (!ra[i]) continue;
+          const int pi = rp[i], qi = rq[i];
+          const double ci = rc[i], si = rs[i];
+          double x = At[pi], y = At[qi];
+          At[pi] = ci * x - si * y;
+          At[qi] = si * x + ci * y;
+          x = Ab[pi];
+          y = Ab[qi];
+          Ab[pi] = ci * x - si * y;
+          Ab[qi] = si * x + ci * y;
         }
-        __syncthreads();
-        // (5) exact 2 x 2 diagonal block of each rotated local pair
-        for (int k = tid; k < nloc; k += kCNT) {
-          if (!la[k]) continue;
-          const int p = lp[k], q = lq[k];
-          double* Ap = colA + tb[k] * st;
-          double* Aq = colA + bb[k] * st;
-          Ap[p] = lapp[k] - lt[k] * lapq[k];
-          Aq[q] = laqq[k] + lt[k] * lapq[k];
-          Ap[q] = 0.0;
-          Aq[p] = 0.0;
+        __syncwarp();
+        if (act && lane == 0) {  // exact 2 x 2 diagonal block
+          At[p] = app - tn * apq;
+          Ab[q] = aqq + tn * apq;
+          At[q] = 0.0;
+          Ab[p] = 0.0;
         }
-        if (tid == 0) {
-          int cnt = 0;
-          for (int i = 0; i < P; ++i) cnt += aa[i];
-          rotations += cnt;
-        }
-        __syncthreads();
+        __syncwarp();
       }
-      // (6) ring move: send the leaving columns to the neighbours' landing buffers
-      // top side: T[g1-1] -> T[g1] of CTA c+1 (T[0] never moves; T[P-1] stays local)
-      // bottom side: Bt[g0] -> Bt[g0-1] of CTA c-1; Bt[0] -> T[1] (CTA 1 when spc == 1)
-      int send_top = -1, send_bot = -1, dst_bot = -1, land_bot = -1;
-      if (nloc > 0) {
-        if (g1 < P && g1 - 1 > 0) send_top = tb[nloc - 1];
-        if (g0 >= 1) { send_bot = bb[0]; dst_bot = crank - 1; land_bot = IN_BOT; }
-        else if (nloc == 1 && P > 1) { send_bot = bb[0]; dst_bot = crank + 1; land_bot = IN_TOP; }
-      }
-      if (send_top >= 0) {
+      // ring move: the top column of the last local slot goes to CTA c+1
+      // (T[0] never moves, T[P-1] stays local as Bt[P-1]); the bottom column of
+      // the first local slot goes to CTA c-1 (Bt[0] -> T[1], at CTA 1 when
+      // spc == 1)
+      if (mine && k == nloc - 1 && g1 < P && g1 - 1 > 0) {
         double* rA = cl.map_shared_rank(colA, crank + 1) + IN_TOP * st;
         double* rV = cl.map_shared_rank(colV, crank + 1) + IN_TOP * st;
-        for (int r = tid; r < n; r += kCNT) {
-          rA[r] = colA[send_top * st + r];
-          rV[r] = colV[send_top * st + r];
+        for (int r = lane; r < n; r += 32) {
+          rA[r] = colA[bt * st + r];
+          rV[r] = colV[bt * st + r];
         }
-        if (tid == 0) cl.map_shared_rank(ids, crank + 1)[IN_TOP] = ids[send_top];
+        if (lane == 0) cl.map_shared_rank(ids, crank + 1)[IN_TOP] = ids[bt];
       }
-      if (send_bot >= 0) {
-        double* rA = cl.map_shared_rank(colA, dst_bot) + land_bot * st;
-        double* rV = cl.map_shared_rank(colV, dst_bot) + land_bot * st;
-        for (int r = tid; r < n; r += kCNT) {
-          rA[r] = colA[send_bot * st + r];
-          rV[r] = colV[send_bot * st + r];
+      if (mine && k == 0 && (g0 >= 1 || (nloc == 1 && P > 1))) {
+        const int dst = g0 >= 1 ? crank - 1 : crank + 1;
+        const int land = g0 >= 1 ? IN_BOT : IN_TOP;
+        double* rA = cl.map_shared_rank(colA, dst) + land * st;
+        double* rV = cl.map_shared_rank(colV, dst) + land * st;
+        for (int r = lane; r < n; r += 32) {
+          rA[r] = colA[bb * st + r];
+          rV[r] = colV[bb * st + r];
         }
-        if (tid == 0) cl.map_shared_rank(ids, dst_bot)[land_bot] = ids[send_bot];
+        if (lane == 0) cl.map_shared_rank(ids, dst)[land] = ids[bb];
       }
       cl.sync();  // columns delivered
-      // (7) relabel: new seating of the local slots, landing buffers copied
-      // into the buffers that were sent away
-      if (tid == 0 && nloc > 0) {
-        int* ntb = nmap;
-        int* nbb = nmap + spc;
-        int* plan = nmap + 2 * spc;  // (landing, target) pairs, up to two
-        int np = 0;
-        int freed[2], nf = 0;
-        if (send_top >= 0) freed[nf++] = send_top;
-        if (send_bot >= 0) freed[nf++] = send_bot;
-        for (int k = nloc - 1; k >= 1; --k) ntb[k] = tb[k - 1];
-        if (g0 == 0) {
-          ntb[0] = tb[0];
-          if (nloc >= 2) ntb[1] = bb[0];
-        } else {
-          const int f = freed[--nf];
-          plan[2 * np] = IN_TOP;
-          plan[2 * np + 1] = f;
-          ++np;
-          ntb[0] = f;
+      // new seating of this warp's slot (computed from the old map, written
+      // to the other parity); landing buffers are copied by the warp that
+      // takes them over
+      if (mine) {
+        int* nm = map + (par ^ 1) * 2 * spc;
+        int ntop, nbot, copy_top = 0, copy_bot = 0;
+        if (k >= 1) ntop = (g0 == 0 && k == 1) ? mp[1] : mp[2 * (k - 1)];
+        else if (g0 == 0) ntop = mp[0];
+        else { ntop = mp[1]; copy_top = 1; }  // old Bt[g0] buffer takes the incoming T[g0]
+        if (k < nloc - 1) nbot = mp[2 * (k + 1) + 1];
+        else if (g1 == P) nbot = mp[2 * (nloc - 1)];
+        else {
+          nbot = (g0 == 0 && nloc == 1) ? mp[1] : mp[2 * (nloc - 1)];
+          copy_bot = 1;
         }
-        for (int k = 0; k < nloc - 1; ++k) nbb[k] = bb[k + 1];
-        if (g1 == P) {
-          nbb[nloc - 1] = tb[nloc - 1];
-        } else {
-          const int f = freed[--nf];
-          plan[2 * np] = IN_BOT;
-          plan[2 * np + 1] = f;
-          ++np;
-          nbb[nloc - 1] = f;
+        if (copy_top) {
+          for (int r = lane; r < n; r += 32) {
+            colA[ntop * st + r] = colA[IN_TOP * st + r];
+            colV[ntop * st + r] = colV[IN_TOP * st + r];
+          }
+          if (lane == 0) ids[ntop] = ids[IN_TOP];
         }
-        for (int k = 0; k < nloc; ++k) {
-          tb[k] = ntb[k];
-          bb[k] = nbb[k];
+        if (copy_bot) {
+          for (int r = lane; r < n; r += 32) {
+            colA[nbot * st + r] = colA[IN_BOT * st + r];
+            colV[nbot * st + r] = colV[IN_BOT * st + r];
+          }
+          if (lane == 0) ids[nbot] = ids[IN_BOT];
         }
-        plan[4] = np;
+        if (lane == 0) {
+          nm[2 * k] = ntop;
+          nm[2 * k + 1] = nbot;
+        }
+        __syncwarp();
       }
-      __syncthreads();
-      if (nloc > 0) {
-        const int* plan = nmap + 2 * spc;
-        const int np = plan[4];
-        for (int e = tid; e < np * n; e += kCNT) {
-          const int j = e / n, r = e % n;
-          const int from = plan[2 * j], to = plan[2 * j + 1];
-          colA[to * st + r] = colA[from * st + r];
-          colV[to * st + r] = colV[from * st + r];
-        }
-        if (tid < np) ids[plan[2 * tid + 1]] = ids[plan[2 * tid]];
-      }
-      __syncthreads();
+      par ^= 1;
+      __syncthreads();  // new seating visible to every warp
     }
   }
 
   // eigenvalues into every CTA's evall
-  for (int lb = tid; lb < 2 * nloc; lb += kCNT) {
-    const int buf = lb < nloc ? tb[lb] : bb[lb - nloc];
+  const int* mp = map + par * 2 * spc;
+  for (int lb = tid; lb < 2 * nloc; lb += blockDim.x) {
+    const int buf = mp[lb];
     const int id = ids[buf];
     if (id >= n) continue;
     const double ev = colA[buf * st + id];
-    for (int c = 0; c < kCS; ++c) cl.map_shared_rank(evall, c)[id] = ev;
+    for (int cc = 0; cc < kCS; ++cc) cl.map_shared_rank(evall, cc)[id] = ev;
   }
   cl.sync();
   double lo = INFINITY, hi = -INFINITY;
-  for (int i = tid; i < n; i += kCNT) {
+  for (int i = tid; i < n; i += blockDim.x) {
     lo = fmin(lo, evall[i]);
     hi = fmax(hi, evall[i]);
   }
-  hi = block_max<kCNT>(hi, shr);
-  lo = -block_max<kCNT>(-lo, shr);
+  // block_max expects 512 threads worth of warps; blockDim is a multiple of 32
+  {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+    }
+    if (lane == 0) {
+      shr[warp] = hi;
+      shr[16 + warp] = lo;
+    }
+    __syncthreads();
+    hi = -INFINITY;
+    lo = INFINITY;
+    for (int w = 0; w < static_cast<int>(blockDim.x) / 32; ++w) {
+      hi = fmax(hi, shr[w]);
+      lo = fmin(lo, shr[16 + w]);
+    }
+  }
   const double add = (lo < hi * kCPdFloor) ? hi * kCPdFloor - lo : 0.0;
   // canonical representative: ascending eigenvalue (ties by index), largest
   // entry of each column positive; one warp per local column
-  const int lane = tid & 31, warp = tid >> 5;
-  for (int lb = warp; lb < 2 * nloc; lb += kCNT / 32) {
-    const int buf = lb < nloc ? tb[lb] : bb[lb - nloc];
+  for (int lb = warp; lb < 2 * nloc; lb += blockDim.x / 32) {
+    const int buf = mp[lb];
     const int id = ids[buf];
     if (id >= n) continue;
     const double e = evall[id];
@@ -387,12 +347,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
   }
   if (crank == 0) {
     if (add != 0.0)
-      for (int i = tid; i < n; i += kCNT) s.C[i + static_cast<long long>(ldn) * i] += add;
+      for (int i = tid; i < n; i += blockDim.x) s.C[i + static_cast<long long>(ldn) * i] += add;
     if (tid == 0) {
-      const int done_sweeps = sweeps;
-      s.eig_sweeps = done_sweeps;
+      s.eig_sweeps = sweeps;
       s.eig_count += 1;
-      s.eig_sweeps_total += done_sweeps;
+      s.eig_sweeps_total += sweeps;
       s.eig_rotations += rotations;
     }
   }
@@ -401,9 +360,9 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(kCNT)
 
 void launch_jacobi_cluster(Search* S, int s0, int s1, int lo_n, int hi_n, int layout_n, cudaStream_t st) {
   if (s1 <= s0 || layout_n <= lo_n) return;
-  const size_t bytes = jacobi_cluster_smem_bytes(layout_n);
-  cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(bytes));
-  k_jacobi_cluster<<<(s1 - s0) * kCS, kCNT, bytes, st>>>(S, s0, lo_n, hi_n, layout_n);
+  const CLayout L = make_layout(layout_n);
+  cudaFuncSetAttribute(k_jacobi_cluster, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(L.bytes));
+  k_jacobi_cluster<<<(s1 - s0) * kCS, L.threads, L.bytes, st>>>(S, s0, lo_n, hi_n, layout_n);
 }
 
 }  // namespace cmaes_gb300
