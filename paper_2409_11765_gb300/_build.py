@@ -10,8 +10,8 @@ LIBDIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(LIBDIR, "libcmaes_gb300.so")
 PROBE_LIB = os.path.join(LIBDIR, "libcmaes_probe.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
-SOURCES = ["kernels_gen.cu", "kernels_eig.cu", "kernels_jacobi_cluster.cu", "kernels_mixed.cu", "capi.cu",
-           "noalloc.cu"]
+SOURCES = ["kernels_gen.cu", "kernels_eig.cu", "kernels_jacobi_cluster.cu", "kernels_mixed.cu",
+           "kernels_eig_mixed.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--extended-lambda", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

@@ -219,6 +219,14 @@ static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
 
 static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap sq = h->tiles(TK_SQUARE, s0, s1);
+  if (h->mixed) {
+    TileMap t32 = h->tiles(TK_SQUARE32, s0, s1);
+    launch_eig_mixed(h->dS, t32, s0, s1, h->max_n, st);
+    if (t32.total > 0) {
+      h->launches += 11;
+      h->phase_launch[kPhaseEig] += 11;
+    }
+  }
   launch_eig_gemm_CB(h->dS, sq, st);
   count_launch(h, kPhaseEig, sq.total);
   launch_eig_gemm_BtT(h->dS, sq, st);
@@ -430,6 +438,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += 3 * align256(n_ * kp * esz);                // BDT QTh QTl
       b += align256(kp * lc * esz) + align256(kp * lc * 4);  // Zm Y32
       b += align256(static_cast<size_t>(ceil_div(n, 256)) * 8);
+      if (n <= eig_mixed_max_n()) b += 2 * align256(n_ * n_ * 4);  // F32a F32b
       b += align256(ldn * lc * 8);                     // X
     } else {
       if (x.cov_nch > 1) b += align256(static_cast<size_t>(tiles_sym(n)) * x.cov_nch * 4096 * 8);
@@ -493,6 +502,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.Zm = take(kp * lc * esz);
       x.Y32 = reinterpret_cast<float*>(take(kp * lc * 4));
       x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(ceil_div(x.n, 256)) * 8));
+      if (x.n <= eig_mixed_max_n()) {
+        x.F32a = reinterpret_cast<float*>(take(n_ * n_ * 4));
+        x.F32b = reinterpret_cast<float*>(take(n_ * n_ * 4));
+      }
     } else {
       x.covpart = x.cov_nch > 1
                       ? reinterpret_cast<double*>(take(static_cast<size_t>(tiles_sym(x.n)) * x.cov_nch * 4096 * 8))
@@ -546,6 +559,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TCOBJ: t = h->mixed ? tiles_tc_objective(x.lam_cap) : 0; break;
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
         case TK_TCSYM: t = h->mixed ? tiles_tc_sym(x.n) : 0; break;
+        case TK_SQUARE32: t = (h->mixed && x.n > 32 && x.n <= eig_mixed_max_n()) ? tiles_square32(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

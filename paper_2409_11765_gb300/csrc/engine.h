@@ -59,6 +59,7 @@ struct Search {
   float *Y32;         // kp x lam_cap, y = B D z from the FP32 accumulators
   double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation
   double fbest64;     // FP64 value of this generation's best point
+  float *F32a, *F32b; // n x n FP32 scratch of the mixed-precision eigensolver route
   int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
@@ -88,7 +89,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_SQUARE32, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -136,6 +137,11 @@ void launch_tc_objective(Search* S, TileMap tm, int precision, cudaStream_t st);
 void launch_tc_cov_partial(Search* S, TileMap tm, int precision, cudaStream_t st);
 void launch_tc_cov_reduce(Search* S, TileMap tm, cudaStream_t st);
 void launch_reeval(Search* S, TileMap tm, cudaStream_t st);
+// mixed-precision eigensolver route (kernels_eig_mixed.cu): FP32 Jacobi
+// sweeps, Newton-Schulz lift to FP64, then the FP64 Jacobi finishes
+int eig_mixed_max_n();
+int tiles_square32(int n);
+void launch_eig_mixed(Search* S, TileMap tm32, int s0, int s1, int max_n, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);

@@ -44,13 +44,17 @@ int jacobi_smem_max_n() {
   return best;
 }
 
+// Searches whose warm start is prepared by the mixed-precision route
+// (kernels_eig_mixed.cu) skip the FP64 B^T C B below.
+__device__ __forceinline__ bool mixed_route(const Search& s) { return s.mixed && s.n > 32 && s.n <= 160; }
+
 // ET = C B (square tiles; only searches whose decomposition is due).
 __global__ void __launch_bounds__(256) k_eig_gemm_CB(Search* S, TileMap tm) {
   __shared__ GemmSmem sm;
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
-  if (s.done || !s.eig_due) return;
+  if (s.done || !s.eig_due || mixed_route(s)) return;
   const int n = s.n, ldn = s.ldn, T = ceil_div(n, kGBM);
   const double* C = s.C;
   const double* B = s.B;
@@ -68,7 +72,7 @@ __global__ void __launch_bounds__(256) k_eig_gemm_BtT(Search* S, TileMap tm) {
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
-  if (s.done || !s.eig_due) return;
+  if (s.done || !s.eig_due || mixed_route(s)) return;
   const int n = s.n, ldn = s.ldn, T = ceil_div(n, kGBM);
   const double* B = s.B;
   const double* ET = s.ET;

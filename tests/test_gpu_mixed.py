@@ -89,6 +89,11 @@ def test_mixed_builtin_generation_sample_and_objective(prec, n, lam, kind):
     # state stays valid; the best point carries its FP64 value
     assert g["gen"] == 4 and np.array_equal(g["C"], g["C"].T)
     assert np.abs(g["B"].T @ g["B"] - np.eye(n)).max() <= 1e-13 * max(n, 10)
+    # the eigendecomposition (FP32 sweeps + FP64 finish on this route) is an
+    # FP64-accurate decomposition of the C it was given
+    recon = (g["B"] * g["D"] ** 2) @ g["B"].T
+    assert rel(recon, g["C"]) <= 1e-12, rel(recon, g["C"])
+    assert np.all(np.diff(g["D"]) >= 0)
     i0 = order[0]
     f_exact = oracle_problem(p)(X[:, i0:i0 + 1])[0]
     assert math.isclose(g["best_f"], f_exact, rel_tol=1e-12, abs_tol=1e-12 * abs(fo).max())
@@ -147,6 +152,8 @@ def test_mixed_ask_tell_update(prec, n, lam):
     dlam = np.linalg.norm(dC, 2) * 1.01 + 1e-12 * (st.D ** 2).max()
     assert np.all(np.abs(g["D"] ** 2 - st.D ** 2) <= dlam)
     assert np.abs(g["B"].T @ g["B"] - np.eye(n)).max() <= 1e-13 * max(n, 10)
+    recon = (g["B"] * g["D"] ** 2) @ g["B"].T
+    assert rel(recon, g["C"]) <= 1e-12, rel(recon, g["C"])
 
 
 @pytest.mark.parametrize("prec", [1, 2])
