@@ -33,7 +33,7 @@ constexpr double kPdFloor = 1e-16;
 // Every kCheckEvery steps all pairs are tested against the rotation threshold
 // at once; when none qualifies no later step would rotate either, so the
 // sweep loop stops there (the same result as a full quiet sweep, sooner).
-constexpr int kCheckEvery = 8;
+constexpr int kCheckEvery = 16;
 
 int jacobi_smem_bytes(int n, bool smem_mats) {
   const int N = n + (n & 1), P = N / 2;
@@ -113,7 +113,6 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   __shared__ double shr[32];
   __shared__ int sh_active;
   __shared__ long long sh_rot;
-  __shared__ int sh_nact;
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due) return;
   const int n = s.n, ldn = s.ldn;
@@ -209,11 +208,26 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         converged = true;
         break;  // uniform over the block (sh_active read after the barrier)
       }
+      if (sh_active && ((r + 1) % kCheckEvery == 0)) {
+        // whole-matrix threshold test (reads only: no rotation of this step
+        // has been applied yet, so it tests the current A)
+        int fail = 0;
+        for (long long e = tid; e < static_cast<long long>(n) * n; e += kJacobiNT) {
+          const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
+          if (i < j) {
+            const double a = A[i + lda * j];
+            if (a != 0.0 && fabs(a) > kJacobiTol * sqrt(fabs(A[i + lda * i] * A[j + lda * j]))) fail = 1;
+          }
+        }
+        if (!__syncthreads_or(fail)) {
+          converged = true;
+          break;
+        }
+      }
       if (tid == 0) {  // rotations applied in this step
         int cnt = 0;
         for (int i = 0; i < P; ++i) cnt += ra[i];
         sh_rot += cnt;
-        sh_nact = cnt;
       }
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;
@@ -263,22 +277,6 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         V[row + lda * q] = sn * vp + c * vq;
       }
       __syncthreads();
-      if (sh_nact * 4 <= P && ((r + 1) % kCheckEvery == 0)) {
-        // few rotations left: whole-matrix threshold test on the updated A;
-        // when nothing qualifies no later step would rotate either
-        int fail = 0;
-        for (long long e = tid; e < static_cast<long long>(n) * n; e += kJacobiNT) {
-          const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
-          if (i < j) {
-            const double a = A[i + lda * j];
-            if (a != 0.0 && fabs(a) > kJacobiTol * sqrt(fabs(A[i + lda * i] * A[j + lda * j]))) fail = 1;
-          }
-        }
-        if (!__syncthreads_or(fail)) {
-          converged = true;
-          break;
-        }
-      }
     }
   }
 

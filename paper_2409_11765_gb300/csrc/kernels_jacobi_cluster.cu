@@ -166,15 +166,48 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
         }
       }
       cl.sync();  // rotation table complete everywhere
-      int nact = 0;
-      for (int i = lane; i < P; i += 32) nact += ra[i];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) nact += __shfl_xor_sync(0xffffffffu, nact, o);
-      const int any = nact > 0;
+      int any = 0;
+      for (int i = lane; i < P; i += 32) any |= ra[i];
+      any = __any_sync(0xffffffffu, any);
       quiet = any ? 0 : quiet + 1;
       if (quiet >= N - 1) {
         converged = true;
         break;  // uniform: every warp of the cluster saw the same table
+      }
+      if (any && ((step + 1) % 16 == 0)) {
+        // whole-matrix threshold test on the current A (this step's
+        // rotations are not applied yet): diagonal to every CTA, each CTA
+        // tests its columns, the verdicts go to every CTA
+        if (mine && lane < 2) {
+          const int buf = lane == 0 ? bt : bb;
+          const int id = ids[buf];
+          if (id < n)
+            for (int cc = 0; cc < kCS; ++cc) cl.map_shared_rank(evall, cc)[id] = colA[buf * st + id];
+        }
+        cl.sync();
+        int fail = 0;
+        if (mine) {
+          for (int h = 0; h < 2; ++h) {
+            const int buf = h == 0 ? bt : bb;
+            const int id = ids[buf];
+            if (id >= n) continue;
+            const double* col = colA + buf * st;
+            for (int r = lane; r < n; r += 32) {
+              const double a = col[r];
+              if (r != id && a != 0.0 && fabs(a) > kCTol * sqrt(fabs(evall[r] * evall[id]))) fail = 1;
+            }
+          }
+        }
+        fail = __syncthreads_or(fail);
+        if (tid < kCS) cl.map_shared_rank(flags, tid)[crank] = fail;
+        cl.sync();
+        int all = 0;
+        for (int cc = 0; cc < kCS; ++cc) all |= flags[cc];
+        cl.sync();  // flags are rewritten by the next test
+        if (!all) {
+          converged = true;
+          break;
+        }
       }
       if (tid == 0 && crank == 0) {  // rotations applied in this step
         int cnt = 0;
@@ -218,41 +251,6 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
           Ab[p] = 0.0;
         }
         __syncwarp();
-      }
-      if (any && nact * 4 <= P && ((step + 1) % 8 == 0)) {
-        // few rotations left: whole-matrix threshold test on the updated A
-        // (diagonal to every CTA, each CTA tests its columns, the verdicts go
-        // to every CTA); when nothing qualifies no later step would rotate
-        if (mine && lane < 2) {
-          const int buf = lane == 0 ? bt : bb;
-          const int id = ids[buf];
-          if (id < n)
-            for (int cc = 0; cc < kCS; ++cc) cl.map_shared_rank(evall, cc)[id] = colA[buf * st + id];
-        }
-        cl.sync();
-        int fail = 0;
-        if (mine) {
-          for (int h = 0; h < 2; ++h) {
-            const int buf = h == 0 ? bt : bb;
-            const int id = ids[buf];
-            if (id >= n) continue;
-            const double* col = colA + buf * st;
-            for (int r = lane; r < n; r += 32) {
-              const double a = col[r];
-              if (r != id && a != 0.0 && fabs(a) > kCTol * sqrt(fabs(evall[r] * evall[id]))) fail = 1;
-            }
-          }
-        }
-        fail = __syncthreads_or(fail);
-        if (tid < kCS) cl.map_shared_rank(flags, tid)[crank] = fail;
-        cl.sync();
-        int all = 0;
-        for (int cc = 0; cc < kCS; ++cc) all |= flags[cc];
-        cl.sync();  // flags are rewritten by the next test
-        if (!all) {
-          converged = true;
-          break;
-        }
       }
       // ring move: the top column of the last local slot goes to CTA c+1
       // (T[0] never moves, T[P-1] stays local as Bt[P-1]); the bottom column of
