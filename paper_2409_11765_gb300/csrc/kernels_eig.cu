@@ -30,10 +30,6 @@ constexpr int kJacobiNT = 512;
 constexpr double kJacobiTol = 1e-14;
 constexpr int kJacobiMaxSweeps = 40;
 constexpr double kPdFloor = 1e-16;
-// Every kCheckEvery steps all pairs are tested against the rotation threshold
-// at once; when none qualifies no later step would rotate either, so the
-// sweep loop stops there (the same result as a full quiet sweep, sooner).
-constexpr int kCheckEvery = 16;
 
 int jacobi_smem_bytes(int n, bool smem_mats) {
   const int N = n + (n & 1), P = N / 2;
@@ -200,34 +196,16 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         rp[i] = p;
         rq[i] = q;
         ra[i] = act;
-        if (act) sh_active = 1;
+        if (act) {
+          sh_active = 1;
+          atomicAdd(reinterpret_cast<unsigned long long*>(&sh_rot), 1ull);
+        }
       }
       __syncthreads();
       quiet = sh_active ? 0 : quiet + 1;
       if (quiet >= N - 1) {
         converged = true;
         break;  // uniform over the block (sh_active read after the barrier)
-      }
-      if (sh_active && ((r + 1) % kCheckEvery == 0)) {
-        // whole-matrix threshold test (reads only: no rotation of this step
-        // has been applied yet, so it tests the current A)
-        int fail = 0;
-        for (long long e = tid; e < static_cast<long long>(n) * n; e += kJacobiNT) {
-          const int i = static_cast<int>(e % n), j = static_cast<int>(e / n);
-          if (i < j) {
-            const double a = A[i + lda * j];
-            if (a != 0.0 && fabs(a) > kJacobiTol * sqrt(fabs(A[i + lda * i] * A[j + lda * j]))) fail = 1;
-          }
-        }
-        if (!__syncthreads_or(fail)) {
-          converged = true;
-          break;
-        }
-      }
-      if (tid == 0) {  // rotations applied in this step
-        int cnt = 0;
-        for (int i = 0; i < P; ++i) cnt += ra[i];
-        sh_rot += cnt;
       }
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;

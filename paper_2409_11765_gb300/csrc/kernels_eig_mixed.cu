@@ -218,20 +218,6 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
         converged = true;
         break;
       }
-      if (sh_active && ((r + 1) % 16 == 0)) {  // whole-matrix threshold test
-        int fail = 0;
-        for (int e = tid; e < n * n; e += kJ32NT) {
-          const int i = e % n, j = e / n;
-          if (i < j) {
-            const float a = fabsf(A[i + lda * j]);
-            if (a > floor_abs && a > kJ32Tol * sqrtf(fabsf(A[i + lda * i] * A[j + lda * j]))) fail = 1;
-          }
-        }
-        if (!__syncthreads_or(fail)) {
-          converged = true;
-          break;
-        }
-      }
       // 2 x 2 block updates of A (blocks P <= Q, mirrored) and V <- V J
       const int nblk = P * (P + 1) / 2;
       for (int b = tid; b < nblk; b += kJ32NT) {

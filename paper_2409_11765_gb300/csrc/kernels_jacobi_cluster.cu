@@ -42,7 +42,7 @@ struct CLayout {
   int stride, nbuf, spc, P, N, threads;
   size_t bytes;
   size_t colA, colV, rc, rs, evall;     // double arrays
-  size_t ids, rp, rq, ra, map, flags;   // int arrays
+  size_t ids, rp, rq, ra, map;          // int arrays
 };
 
 __host__ __device__ inline CLayout make_layout(int max_n) {
@@ -65,7 +65,6 @@ __host__ __device__ inline CLayout make_layout(int max_n) {
   L.rq = i; i += L.P;
   L.ra = i; i += L.P;
   L.map = i; i += 4 * L.spc;  // two parities x (top, bottom) buffer of each local slot
-  L.flags = i; i += kCS;      // per-CTA results of the whole-matrix threshold test
   L.bytes = d * 8 + i * 4 + 16;
   return L;
 }
@@ -97,7 +96,6 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
   int* rq = ibase + L.rq;
   int* ra = ibase + L.ra;
   int* map = ibase + L.map;  // map[par * 2 spc + 2 k] = top buffer, +1 = bottom buffer
-  int* flags = ibase + L.flags;
 
   const int n = s.n, ldn = s.ldn;
   const int N = n + (n & 1), P = N / 2;
@@ -169,50 +167,15 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
       int any = 0;
       for (int i = lane; i < P; i += 32) any |= ra[i];
       any = __any_sync(0xffffffffu, any);
+      if (tid == 0 && crank == 0) {
+        int cnt = 0;
+        for (int i = 0; i < P; ++i) cnt += ra[i];
+        rotations += cnt;
+      }
       quiet = any ? 0 : quiet + 1;
       if (quiet >= N - 1) {
         converged = true;
         break;  // uniform: every warp of the cluster saw the same table
-      }
-      if (any && ((step + 1) % 16 == 0)) {
-        // whole-matrix threshold test on the current A (this step's
-        // rotations are not applied yet): diagonal to every CTA, each CTA
-        // tests its columns, the verdicts go to every CTA
-        if (mine && lane < 2) {
-          const int buf = lane == 0 ? bt : bb;
-          const int id = ids[buf];
-          if (id < n)
-            for (int cc = 0; cc < kCS; ++cc) cl.map_shared_rank(evall, cc)[id] = colA[buf * st + id];
-        }
-        cl.sync();
-        int fail = 0;
-        if (mine) {
-          for (int h = 0; h < 2; ++h) {
-            const int buf = h == 0 ? bt : bb;
-            const int id = ids[buf];
-            if (id >= n) continue;
-            const double* col = colA + buf * st;
-            for (int r = lane; r < n; r += 32) {
-              const double a = col[r];
-              if (r != id && a != 0.0 && fabs(a) > kCTol * sqrt(fabs(evall[r] * evall[id]))) fail = 1;
-            }
-          }
-        }
-        fail = __syncthreads_or(fail);
-        if (tid < kCS) cl.map_shared_rank(flags, tid)[crank] = fail;
-        cl.sync();
-        int all = 0;
-        for (int cc = 0; cc < kCS; ++cc) all |= flags[cc];
-        cl.sync();  // flags are rewritten by the next test
-        if (!all) {
-          converged = true;
-          break;
-        }
-      }
-      if (tid == 0 && crank == 0) {  // rotations applied in this step
-        int cnt = 0;
-        for (int i = 0; i < P; ++i) cnt += ra[i];
-        rotations += cnt;
       }
       if (mine && any) {
         double* At = colA + bt * st;
