@@ -438,6 +438,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += 3 * align256(n_ * kp * esz);                // BDT QTh QTl
       b += align256(kp * lc * esz) + align256(kp * lc * 4);  // Zm Y32
       b += align256(static_cast<size_t>(ceil_div(n, 256)) * 8);
+      b += align256(n_ * 4);                             // lam32
+      b += align256(static_cast<size_t>(x.mu_cap) * 4);  // w32
       if (n <= eig_mixed_max_n()) b += 2 * align256(n_ * n_ * 4);  // F32a F32b
       b += align256(ldn * lc * 8);                     // X
     } else {
@@ -502,6 +504,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.Zm = take(kp * lc * esz);
       x.Y32 = reinterpret_cast<float*>(take(kp * lc * 4));
       x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(ceil_div(x.n, 256)) * 8));
+      x.lam32 = reinterpret_cast<float*>(take(n_ * 4));
+      x.w32 = reinterpret_cast<float*>(take(static_cast<size_t>(x.mu_cap) * 4));
       if (x.n <= eig_mixed_max_n()) {
         x.F32a = reinterpret_cast<float*>(take(n_ * n_ * 4));
         x.F32b = reinterpret_cast<float*>(take(n_ * n_ * 4));

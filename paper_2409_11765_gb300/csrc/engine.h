@@ -55,6 +55,8 @@ struct Search {
   int mixed, kp, covm_kc, covm_nch;
   void *BDT;          // n x kp, row i = (B diag(D))(i, :), input format (TF32 / BF16)
   void *QTh, *QTl;    // n x kp, row i = Q(i, :), hi and lo parts
+  float *lam32;       // n: Lambda in FP32 for the tensor-core objective epilogue
+  float *w32;         // mu_cap: recombination weights in FP32 for the rank-mu staging
   void *Zm;           // kp x lam_cap, z in input format (candidate columns)
   float *Y32;         // kp x lam_cap, y = B D z from the FP32 accumulators
   double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation

@@ -149,7 +149,7 @@ __global__ void __launch_bounds__(256) k_eig_copy_b(Search* S, TileMap tm) {
 
 // FP32 cyclic Jacobi on A32 (F32a, symmetrised on load) with V32 = I; V32 is
 // written to F32b. Rotations below FP32 resolution are skipped: a pair turns
-// only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 4 eps32 max|a_ii|.
+// only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
 __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
   extern __shared__ float fsm[];
   __shared__ int sh_active;
@@ -180,7 +180,8 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
     sh_amax = m;
   }
   __syncthreads();
-  const float floor_abs = 4.f * 1.1920929e-7f * sh_amax;
+  // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
+  const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
   int quiet = 0;
   bool converged = false;
   for (int sweep = 0; sweep < kJ32MaxSweeps && !converged; ++sweep) {

@@ -59,6 +59,7 @@ __device__ void compute_params(Search& s, const DevOptions& o, double* sh) {
   for (int i = threadIdx.x; i < mu; i += NT) {
     const double wi = (lw - log(static_cast<double>(i + 1))) / sum;
     s.w[i] = wi;
+    if (s.mixed) s.w32[i] = static_cast<float>(wi);
     sq += wi * wi;
   }
   const double ssq = block_sum<NT>(sq, sh);

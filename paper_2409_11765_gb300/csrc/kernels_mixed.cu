@@ -6,7 +6,12 @@
 //   k_tc_objective  U^T = (X - x*)^T Q^T with 3-term split operands
 //                   (hi*hi + hi*lo + lo*hi, about 22 significant bits), x - x*
 //                   formed in FP64; each thread owns one candidate and sums
-//                   its objective terms in FP64 straight from TMEM.
+//                   its objective terms straight from TMEM in FP32 (Kahan
+//                   summation): Lambda_i u_i^2 for the ellipsoid, and for the
+//                   Rastrigin u_i^2 + 20 sin^2(pi u_i), which equals
+//                   u_i^2 - 10 cos(2 pi u_i) + 10 and keeps its relative
+//                   accuracy near the optimum (GB300's FP64 pipe is 1/64 of
+//                   the FP32 one, so FP64 transcendentals here would dominate).
 //   k_tc_cov_*      the rank-mu sum of Eq. (3), sum_r w_r y_r y_r^T, with split
 //                   operands (the FP32-accuracy correction term), upper
 //                   128 x 128 tiles, rank chunks added in order in FP64.
@@ -74,6 +79,7 @@ __global__ void __launch_bounds__(256) k_tc_prepare_q(Search* S, int si) {
     if (k < n) tc_split<KIND>(s.Q[i + static_cast<long long>(ldn) * k], h, l);
     qh[e] = h;
     ql[e] = l;
+    if (k == 0) s.lam32[i] = static_cast<float>(s.lamdiag[i]);
   }
 }
 
@@ -210,7 +216,9 @@ __global__ void __launch_bounds__(256, 1) k_tc_objective(Search* S, TileMap tm) 
   const double* xs = s.xstar;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int quarter = warp & 3, half = warp >> 2;
-  double facc = 0.0;
+  float facc = 0.0f, fcomp = 0.0f;  // Kahan sum
+  const float* lam32 = s.lam32;
+  const bool ellipsoid = s.obj == 1;
   bool ok = true;
   for (int r0 = 0; r0 < n && ok; r0 += 256) {
     const int nt = min(256, ((n - r0 + 15) / 16) * 16);
@@ -220,9 +228,9 @@ __global__ void __launch_bounds__(256, 1) k_tc_objective(Search* S, TileMap tm) 
         Vec16<KIND> h, l;
 #pragma unroll
         for (int q = 0; q < epv; ++q) {
-          double d = 0.0;
-          if (j < lam_cap && k + q < n) d = X[(k + q) + static_cast<long long>(ldn) * j] - xs[k + q];
-          tc_split<KIND>(d, h.v[q], l.v[q]);
+          float d = 0.0f;  // x - x* formed in FP64, split in FP32
+          if (j < lam_cap && k + q < n) d = static_cast<float>(X[(k + q) + static_cast<long long>(ldn) * j] - xs[k + q]);
+          tc_split32<KIND>(d, h.v[q], l.v[q]);
         }
         *reinterpret_cast<Vec16<KIND>*>(a_hi + tc_off<KIND>(r, v * epv)) = h;
         *reinterpret_cast<Vec16<KIND>*>(a_lo + tc_off<KIND>(r, v * epv)) = l;
@@ -249,22 +257,28 @@ __global__ void __launch_bounds__(256, 1) k_tc_objective(Search* S, TileMap tm) 
       for (int q = 0; q < 16; ++q) {
         const int i = r0 + c + q;
         if (i < n) {
-          const double u = static_cast<double>(v[q]);
-          facc += (s.obj == 1) ? s.lamdiag[i] * u * u
-                               : u * u - 10.0 * cos((2.0 * 3.141592653589793) * u);
+          const float u = v[q];
+          float term;
+          if (ellipsoid) {
+            term = lam32[i] * u * u;
+          } else {
+            const float sp = sinpif(u);
+            term = u * u + 20.0f * sp * sp;
+          }
+          const float y = term - fcomp;
+          const float t2 = facc + y;
+          fcomp = (t2 - facc) - y;
+          facc = t2;
         }
       }
     }
     tc_tile_done();
   }
-  fsum[half][quarter * 32 + lane] = facc;
+  fsum[half][quarter * 32 + lane] = static_cast<double>(facc) - static_cast<double>(fcomp);
   __syncthreads();
   if (ok && half == 0) {
     const int j = j0 + quarter * 32 + lane;
-    if (j < lam) {
-      const double f = fsum[0][quarter * 32 + lane] + fsum[1][quarter * 32 + lane];
-      s.f[j] = (s.obj == 2) ? 10.0 * n + f : f;
-    }
+    if (j < lam) s.f[j] = fsum[0][quarter * 32 + lane] + fsum[1][quarter * 32 + lane];
   }
   tc_end(ctx);
   if (!ok && threadIdx.x == 0) atomicOr(s.err, 1);
@@ -305,7 +319,7 @@ __global__ void __launch_bounds__(256, 1) k_tc_cov_partial(Search* S, TileMap tm
   tc_begin(ctx, dyn, mbar, &tslot);
   constexpr int epv = Vec16<KIND>::epv;
   const float* Y = s.Y32;
-  const double* w = s.w;
+  const float* w = s.w32;
   const int* order = s.order;
   auto stage = [&](int k0, unsigned char* a_hi, unsigned char* a_lo, unsigned char* b_hi, unsigned char* b_lo) {
     // element (row, rank): rows run over lanes so that each load of a
@@ -317,14 +331,14 @@ __global__ void __launch_bounds__(256, 1) k_tc_cov_partial(Search* S, TileMap tm
 #pragma unroll
       for (int q = 0; q < epv; ++q) {
         const int rk = k_lo + k0 + v * epv + q;
-        double ya = 0.0, yb = 0.0;
+        float ya = 0.0f, yb = 0.0f;
         if (rk < k_hi) {
           const long long col = static_cast<long long>(order[rk]) * kp;
-          if (ia < n) ya = w[rk] * static_cast<double>(Y[col + ia]);
-          if (ib < n) yb = static_cast<double>(Y[col + ib]);
+          if (ia < n) ya = w[rk] * Y[col + ia];
+          if (ib < n) yb = Y[col + ib];
         }
-        tc_split<KIND>(ya, ah.v[q], al.v[q]);
-        tc_split<KIND>(yb, bh.v[q], bl.v[q]);
+        tc_split32<KIND>(ya, ah.v[q], al.v[q]);
+        tc_split32<KIND>(yb, bh.v[q], bl.v[q]);
       }
       *reinterpret_cast<Vec16<KIND>*>(a_hi + tc_off<KIND>(r, v * epv)) = ah;
       *reinterpret_cast<Vec16<KIND>*>(a_lo + tc_off<KIND>(r, v * epv)) = al;

@@ -126,6 +126,14 @@ __device__ __forceinline__ uint32_t tc_off(int r, int k) {
   return static_cast<uint32_t>(((r >> 3) * kcores + ((k * esz) >> 4)) * 128 + (r & 7) * 16 + ((k * esz) & 15));
 }
 
+// Split a float into hi + lo in the input format; x - hi is exact in FP32, so
+// hi + lo carries 22 (TF32) or 16 (BF16) significant bits of x.
+template <int KIND>
+__device__ __forceinline__ void tc_split32(float x, typename TcElem<KIND>::T& hi, typename TcElem<KIND>::T& lo) {
+  hi = TcElem<KIND>::from(x);
+  lo = TcElem<KIND>::from(x - TcElem<KIND>::back(hi));
+}
+
 // Split x into hi + lo in the input format (hi = round(x), lo = round(x - hi)).
 template <int KIND>
 __device__ __forceinline__ void tc_split(double x, typename TcElem<KIND>::T& hi, typename TcElem<KIND>::T& lo) {
