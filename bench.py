@@ -53,8 +53,8 @@ def parse_args():
 
 
 def dist_env():
-    return (int(os.environ.get("RANK", "0")), int(os.environ.get("LOCAL_RANK", "0")),
-            int(os.environ.get("WORLD_SIZE", "1")))
+    from paper_2409_11765_gb300 import dist as D
+    return D.env()
 
 
 def workload():
@@ -230,8 +230,9 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
                                     box_lo=wl.box_lo, box_hi=wl.box_hi, max_restarts=255,
                                     ipop_double=0)
     ns = [s.n for s in wl.searches]
+    from paper_2409_11765_gb300 import dist as D
     h = eng.cmaes_create_batch(ns, [s.lam for s in wl.searches], [s.x0 for s in wl.searches],
-                               [s.sigma0 for s in wl.searches], 20240918 + 7919 * rank, opt)
+                               [s.sigma0 for s in wl.searches], D.rank_seed(20240918, rank), opt)
     try:
         for i, s in enumerate(wl.searches):
             p = s.problem
@@ -273,11 +274,8 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
         launches = eng.cmaes_kernel_launches(h) - launches0
         eng.cmaes_set_profiling(h, False)
         phase_ms, _ = eng.cmaes_phase_times(h, reset=True)
-        total_ms = sum(a.elapsed_time(b) for a, b in zip(starts, ends))
-        if dist is not None:
-            t = torch.tensor([total_ms], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            total_ms = float(t.item())
+        total_ms = D.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), dist,
+                                    device="cuda")
         eig1 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
         dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
         rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
@@ -297,7 +295,7 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
     n = ns[0]
     flops = phase_flops(wl, prec_name, eig_flops(n, rot, dec) / args.steps)
     return {
-        "value": cand * args.steps * world / (total_ms / 1e3),
+        "value": D.whole_job_rate(cand, args.steps, world, total_ms),
         "ms_per_step": total_ms / args.steps,
         "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
         "phase_flops_per_step": flops,
