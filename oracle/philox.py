@@ -101,6 +101,22 @@ def normals(seed, search, restart, gen, n, lam):
     return np.where(even, r * np.cos(a), r * np.sin(a))
 
 
+def normals_columns(seed, search, restart, gen, n, cols):
+    """Columns `cols` of normals(seed, search, restart, gen, n, lam): the same
+    counters, for when only a few candidates are needed."""
+    k0, k1 = seed_key(seed)
+    i = np.arange(n, dtype=np.uint64)[:, None]
+    k = np.asarray(cols, dtype=np.uint64)[None, :]
+    w0, w1, w2, w3 = philox4x32_10(i >> np.uint64(1), k, gen,
+                                   stream_word(search, restart), k0, k1)
+    u1 = uniform_from_words(w0, w1)
+    u2 = uniform_from_words(w2, w3)
+    r = np.sqrt(-2.0 * np.log(u1))
+    a = (2.0 * np.pi) * u2
+    even = (np.arange(n) % 2 == 0)[:, None]
+    return np.where(even, r * np.cos(a), r * np.sin(a))
+
+
 def restart_mean(seed, search, restart, n, lo, hi):
     """Initial mean of descent `restart`: uniform in the box [lo, hi]^n."""
     k0, k1 = seed_key(seed)

@@ -91,3 +91,9 @@ def test_restart_mean_in_box_and_uniform():
     assert np.all(m > -5.0) and np.all(m < 5.0)
     assert stats.kstest((m + 5.0) / 10.0, "uniform").pvalue > 1e-4
     assert not np.array_equal(m, philox.restart_mean(5, 2, 4, 20000, -5.0, 5.0))
+
+
+def test_normals_columns_match_full_draw():
+    full = philox.normals(3, 2, 1, 7, 9, 40)
+    cols = [0, 5, 39, 17]
+    assert np.array_equal(philox.normals_columns(3, 2, 1, 7, 9, cols), full[:, cols])
