@@ -555,14 +555,14 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_ROWS: t = tiles_rows(x.n); break;
         case TK_RECOMB: t = tiles_recomb(x.n, x.mu_cap); break;
         case TK_GEMV: t = tiles_gemv(x.n); break;
-        case TK_SYM: t = tiles_sym(x.n); break;
+        case TK_SYM: t = 4 * tiles_sym(x.n); break;  // reduce: 4 blocks per tile
         case TK_SQUARE: t = tiles_square(x.n); break;
         case TK_COVP: t = tiles_sym(x.n) * x.cov_nch; break;
         case TK_RANK2D: t = tiles_rank2d(x.lam_cap); break;
         case TK_TCSAMPLE: t = h->mixed ? tiles_tc_sample(x.n, x.lam_cap) : 0; break;
         case TK_TCOBJ: t = h->mixed ? tiles_tc_objective(x.lam_cap) : 0; break;
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
-        case TK_TCSYM: t = h->mixed ? tiles_tc_sym(x.n) : 0; break;
+        case TK_TCSYM: t = h->mixed ? 16 * tiles_tc_sym(x.n) : 0; break;  // reduce: 16 blocks per tile
         case TK_SQUARE32: t = (h->mixed && x.n > 32 && x.n <= eig_mixed_max_n()) ? tiles_square32(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);

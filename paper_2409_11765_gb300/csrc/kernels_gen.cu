@@ -154,8 +154,23 @@ __global__ void __launch_bounds__(256) k_sample_z(Search* S, TileMap tm, DevOpti
   const int k = static_cast<int>(e / npairs), j = static_cast<int>(e % npairs);
   if (k >= lam) return;
   double z0, z1;
-  normal_pair(static_cast<uint32_t>(j), static_cast<uint32_t>(k), static_cast<uint32_t>(s.gen),
-              stream_word(s.index, s.restart), o.key0, o.key1, z0, z1);
+  if (s.mixed) {
+    // the values are rounded to TF32 / BF16 right after: FP32 Box-Muller on
+    // the same 52-bit uniforms (FP64 log and sincos would dominate on GB300)
+    const uint4 w = philox4x32_10(make_uint4(static_cast<uint32_t>(j), static_cast<uint32_t>(k),
+                                             static_cast<uint32_t>(s.gen), stream_word(s.index, s.restart)),
+                                  o.key0, o.key1);
+    const float u1 = static_cast<float>(uniform52(w.x, w.y));
+    const float u2 = static_cast<float>(uniform52(w.z, w.w));
+    const float r = sqrtf(-2.0f * logf(u1));
+    float sn, cs;
+    sincospif(2.0f * u2, &sn, &cs);
+    z0 = r * cs;
+    z1 = r * sn;
+  } else {
+    normal_pair(static_cast<uint32_t>(j), static_cast<uint32_t>(k), static_cast<uint32_t>(s.gen),
+                stream_word(s.index, s.restart), o.key0, o.key1, z0, z1);
+  }
   if (j == 0) s.rank[k] = 0;  // k_rank accumulates into it
   if (s.mixed) {
     // z in the tensor-core input format; the recombination reads the same values
@@ -283,10 +298,18 @@ void launch_colreduce_f(Search* S, TileMap tm, cudaStream_t st) {
 // split into chunks of kRankChunk handled by separate blocks that add their
 // integer counts atomically (integer sums do not depend on the order).
 // rank[] is cleared by k_sample_z (the ask/tell path also samples first).
-__device__ __forceinline__ double rank_key(double f) { return isnan(f) ? INFINITY : f; }
+// Order-preserving 64-bit integer key of f: NaN -> +inf, -0 -> +0, then the
+// IEEE bit pattern with the sign folded so that unsigned order = numeric order.
+// (Comparing integers keeps the O(lambda^2) count off GB300's slow FP64 pipe.)
+__device__ __forceinline__ unsigned long long rank_key(double f) {
+  if (isnan(f)) f = INFINITY;
+  if (f == 0.0) f = 0.0;
+  const unsigned long long b = static_cast<unsigned long long>(__double_as_longlong(f));
+  return (b >> 63) ? ~b : (b | 0x8000000000000000ull);
+}
 
 __global__ void __launch_bounds__(256) k_rank(Search* S, TileMap tm) {
-  __shared__ double keys[kRankChunk];
+  __shared__ unsigned long long keys[kRankChunk];
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
@@ -302,12 +325,12 @@ __global__ void __launch_bounds__(256) k_rank(Search* S, TileMap tm) {
   for (int q = threadIdx.x; q < jn; q += 256) keys[q] = rank_key(f[j0 + q]);
   __syncthreads();
   if (k >= lam) return;
-  const double key = rank_key(f[k]);
+  const unsigned long long key = rank_key(f[k]);
   int cnt = 0;
-  for (int jj = 0; jj < jn; ++jj) {
-    const double kj = keys[jj];
-    cnt += (kj < key) || (kj == key && j0 + jj < k);
-  }
+  // candidates j < k count when key_j <= key_k, candidates j > k when key_j < key_k
+  const int split = min(max(k - j0, 0), jn);
+  for (int jj = 0; jj < split; ++jj) cnt += keys[jj] <= key;
+  for (int jj = split; jj < jn; ++jj) cnt += keys[jj] < key;
   if (cnt) atomicAdd(&s.rank[k], cnt);
 }
 
@@ -579,12 +602,14 @@ __global__ void __launch_bounds__(256) k_cov_reduce(Search* S, TileMap tm) {
   if (s.done || s.cov_nch == 1) return;
   const int n = s.n, ldn = s.ldn, nch = s.cov_nch;
   const int used = ceil_div(s.mu, s.cov_kc);
+  const int sub = t & 3;  // a quarter of the tile per block
+  t >>= 2;
   int ti, tj;
   sym_tile(t, n, ti, tj);
   const double c1 = s.c1, cmu = s.cmu;
   const double a = 1.0 - c1 - cmu + c1 * (1.0 - s.hsig) * s.cc * (2.0 - s.cc);
   const double* part = s.covpart + static_cast<long long>(t) * nch * (kGBM * kGBN);
-  for (int e = threadIdx.x; e < kGBM * kGBN; e += 256) {
+  for (int e = sub * 1024 + threadIdx.x; e < (sub + 1) * 1024; e += 256) {
     const int ii = e & (kGBM - 1), jj = e >> 6;
     const int i = ti * kGBM + ii, j = tj * kGBN + jj;
     if (i >= n || j >= n || i > j) continue;

@@ -385,12 +385,14 @@ __global__ void __launch_bounds__(256) k_tc_cov_reduce(Search* S, TileMap tm) {
   if (s.done) return;
   const int n = s.n, ldn = s.ldn, nch = s.covm_nch;
   const int used = ceil_div(s.mu, s.covm_kc);
+  const int sub = t & 15;  // a sixteenth of the tile per block
+  t >>= 4;
   int ti, tj;
   sym_tile128(t, n, ti, tj);
   const double c1 = s.c1, cmu = s.cmu;
   const double a = 1.0 - c1 - cmu + c1 * (1.0 - s.hsig) * s.cc * (2.0 - s.cc);
   const double* part = s.covpart + static_cast<long long>(t) * nch * (128 * 128);
-  for (int e = threadIdx.x; e < 128 * 128; e += 256) {
+  for (int e = sub * 1024 + threadIdx.x; e < (sub + 1) * 1024; e += 256) {
     const int r = e & 127, cc = e >> 7;
     const int i = ti * 128 + r, j = tj * 128 + cc;
     if (i >= n || j >= n || i > j) continue;
