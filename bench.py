@@ -280,6 +280,7 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
         dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
         rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
         swp = sum(b["sweeps"] - a["sweeps"] for a, b in zip(eig0, eig1))
+        swp32 = sum(b["sweeps32"] - a["sweeps32"] for a, b in zip(eig0, eig1))
         torch.cuda.set_stream(torch.cuda.default_stream())
         # e2e through the public API: one generation and a host read of every
         # search's best point and value, synchronised each step
@@ -300,7 +301,7 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
         "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
         "phase_flops_per_step": flops,
         "gpu_launches": int(launches),
-        "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot},
+        "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot, "sweeps_fp32": swp32},
         "e2e": {"value": cand * args.e2e_steps * world / e2e_el, "unit": UNIT,
                 "h2d_bytes_per_step": 0, "d2h_bytes_per_step": sum(8 * m + 8 for m in ns)},
         "clocks": clocks,

@@ -210,10 +210,12 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches,
                                int reset);
 
 /* Work done by the eigensolver of search s since creation: decompositions,
- * Jacobi sweeps and plane rotations applied (any pointer may be NULL).
- * Synchronises. */
+ * FP64 Jacobi sweeps, plane rotations applied by them, and the FP32 Jacobi
+ * sweeps that precondition them on mixed-precision handles (zero on FP64
+ * handles). Any pointer may be NULL. Synchronises. */
 cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions,
-                             long long* sweeps, long long* rotations);
+                             long long* sweeps, long long* rotations,
+                             long long* sweeps32);
 
 /* Number of kernel launches issued by the handle since creation. */
 long long cmaes_kernel_launches(cmaes_t h);

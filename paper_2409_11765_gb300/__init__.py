@@ -101,9 +101,7 @@ def lib():
         "cmaes_set_profiling": (I, [H, I]),
         "cmaes_phase_times": (I, [H, _DP, ctypes.POINTER(ctypes.c_longlong), I]),
         "cmaes_kernel_launches": (ctypes.c_longlong, [H]),
-        "cmaes_eig_stats": (I, [H, I, ctypes.POINTER(ctypes.c_longlong),
-                                ctypes.POINTER(ctypes.c_longlong),
-                                ctypes.POINTER(ctypes.c_longlong)]),
+        "cmaes_eig_stats": (I, [H, I] + [ctypes.POINTER(ctypes.c_longlong)] * 4),
         "cmaes_evaluate_noalloc": (I, [I, I, I, V, I, V, I, V, V, V, V]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
@@ -298,9 +296,9 @@ def cmaes_phase_times(h, reset=False):
 
 
 def cmaes_eig_stats(h, s):
-    v = [ctypes.c_longlong() for _ in range(3)]
+    v = [ctypes.c_longlong() for _ in range(4)]
     _check(h, lib().cmaes_eig_stats(h, s, *[ctypes.byref(x) for x in v]))
-    return dict(zip(("decompositions", "sweeps", "rotations"), (x.value for x in v)))
+    return dict(zip(("decompositions", "sweeps", "rotations", "sweeps32"), (x.value for x in v)))
 
 
 def probe_fma_tflops(precision=64, blocks_per_sm=4, repeats=5):

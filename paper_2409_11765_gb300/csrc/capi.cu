@@ -887,7 +887,7 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches, int r
 }
 
 cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions, long long* sweeps,
-                             long long* rotations) {
+                             long long* rotations, long long* sweeps32) {
   CHECK_HANDLE(h);
   CHECK_SEARCH(h, s);
   Search cur;
@@ -896,6 +896,7 @@ cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions, long l
   if (decompositions) *decompositions = cur.eig_count;
   if (sweeps) *sweeps = cur.eig_sweeps_total;
   if (rotations) *rotations = cur.eig_rotations;
+  if (sweeps32) *sweeps32 = cur.eig_sweeps32;
   return CMAES_OK;
 }
 

@@ -201,4 +201,61 @@ __device__ __forceinline__ void gemm_tile_f64(int M, int N, int K, int i0, int j
     }
 }
 
+// ---------------------------------------------------------------------------
+// Plane rotation of the cyclic Jacobi method for the symmetric 2 x 2 block
+// [[app, apq], [apq, aqq]] (Golub & Van Loan, Matrix Computations, §8.5):
+// t = tan(phi) is the root of smaller magnitude of apq t^2 + d t - apq = 0 with
+// d = aqq - app (t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), theta = d / (2 apq)),
+// c = 1 / sqrt(1 + t^2), s = t c, and the rotated block is
+// diag(app - t apq, aqq + t apq).
+//
+// GB300 runs FP64 at 1/64 of the FP32 rate and an FP64 divide or square root
+// expands into a long sequence on that pipe, so t and c start from FP32 values
+// and are finished in FP64 by Newton's method:
+//   t: two steps on g(t) = apq t^2 + d t - apq with an FP32 reciprocal of g'(t)
+//      (each step multiplies the relative error by about 2^-22);
+//   c: two steps of y <- y (3 - x y^2) / 2 on x = 1 + t^2, Newton's iteration
+//      for 1/y^2 = x (each step squares the relative error).
+// d and apq are first scaled by a power of two (exactly) so that the larger of
+// the two lies in [1, 4): the FP32 values neither overflow nor underflow.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void jacobi_rotation(double app, double aqq, double apq, double& t,
+                                                double& c, double& s) {
+  const double d = aqq - app;
+  const double mx = fmax(fabs(d), fabs(apq));
+  const int e = static_cast<int>((__double_as_longlong(mx) >> 52) & 0x7ff);
+  const double sc = __longlong_as_double(static_cast<long long>(2046 - min(e, 2045)) << 52);
+  const double ds = d * sc, as = apq * sc;
+  const float df = static_cast<float>(ds), af = static_cast<float>(as);
+  float tf;
+  if (fabsf(af) * 0x1p40f < fabsf(df)) {
+    tf = __fdividef(af, df);  // |theta| > 2^39: t = 1 / (2 theta) to FP32 precision
+  } else {
+    const float th = __fdividef(df, af + af);
+    tf = __fdividef(th >= 0.f ? 1.f : -1.f, fabsf(th) + sqrtf(fmaf(th, th, 1.f)));
+  }
+  double tt = static_cast<double>(tf);
+  const double as2 = as + as;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const double g = fma(fma(as, tt, ds), tt, -as);
+    const double r = static_cast<double>(__fdividef(1.f, static_cast<float>(fma(as2, tt, ds))));
+    tt = fma(-g, r, tt);
+  }
+  const double x = fma(tt, tt, 1.0), hx = 0.5 * x;
+  double y = static_cast<double>(rsqrtf(static_cast<float>(x)));
+#pragma unroll
+  for (int it = 0; it < 2; ++it) y = fma(y, fma(-hx * y, y, 0.5), y);
+  t = tt;
+  c = y;
+  s = tt * y;
+}
+
+// Rotation test of the cyclic Jacobi method: the pair turns when
+// |apq| > tol sqrt(|app aqq|), evaluated as apq^2 > tol^2 |app aqq| (the same
+// test without an FP64 square root for entries between 1e-150 and 1e150).
+__device__ __forceinline__ bool jacobi_rotates(double app, double aqq, double apq, double tol2) {
+  return apq != 0.0 && apq * apq > tol2 * fabs(app * aqq);
+}
+
 }  // namespace cmaes_gb300

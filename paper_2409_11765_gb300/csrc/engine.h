@@ -49,8 +49,9 @@ struct Search {
   double sigma, best_f, mueff, cs, ds, cc, c1, cmu, chin, psnorm, hsig;
   int lam, mu, gen, restart, g_eig, hist_len, max_iter, hist_count;
   int done, flags, eig_due, eig_sweeps, pad_;
-  // eigensolver work counters (decompositions, sweeps, rotations applied)
-  long long eig_count, eig_sweeps_total, eig_rotations;
+  // eigensolver work counters (decompositions, FP64 sweeps, rotations applied,
+  // FP32 sweeps of the mixed-precision route)
+  long long eig_count, eig_sweeps_total, eig_rotations, eig_sweeps32;
   // mixed precision (precision != FP64): tensor-core operands, K padded to kp
   int mixed, kp, covm_kc, covm_nch;
   void *BDT;          // n x kp, row i = (B diag(D))(i, :), input format (TF32 / BF16)

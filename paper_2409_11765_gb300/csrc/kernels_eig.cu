@@ -9,7 +9,9 @@
 //      The rotation zeroing a_pq uses theta = (a_qq - a_pp) / (2 a_pq),
 //      t = sgn(theta) / (|theta| + sqrt(theta^2 + 1)), c = 1/sqrt(1 + t^2),
 //      s = t c (Golub & Van Loan, §8.5), and is skipped when
-//      |a_pq| <= tol sqrt(|a_pp a_qq|) (a relative threshold).
+//      |a_pq| <= tol sqrt(|a_pp a_qq|) (a relative threshold); both are
+//      evaluated by jacobi_rotation / jacobi_rotates (device_common.cuh),
+//      which keep FP64 divides and square roots off the critical path.
 //   3. A <- J^T A J is applied per 2 x 2 block (pair P rows, pair Q columns);
 //      only blocks with P <= Q are computed and mirrored, so A stays
 //      symmetric. B <- B J accumulates the rotations into the eigenbasis.
@@ -181,12 +183,8 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         int act = 0;
         if (p < n && q < n) {
           const double app = A[p + lda * p], aqq = A[q + lda * q], apq = A[p + lda * q];
-          if (apq != 0.0 && fabs(apq) > kJacobiTol * sqrt(fabs(app * aqq))) {
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double at = fabs(theta);
-            tn = (at > 1e150) ? 0.5 / theta : (theta >= 0.0 ? 1.0 : -1.0) / (at + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(tn * tn + 1.0);
-            sn = tn * c;
+          if (jacobi_rotates(app, aqq, apq, kJacobiTol * kJacobiTol)) {
+            jacobi_rotation(app, aqq, apq, tn, c, sn);
             act = 1;
           }
         }

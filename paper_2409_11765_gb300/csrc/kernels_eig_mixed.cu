@@ -182,9 +182,9 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
   __syncthreads();
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
-  int quiet = 0;
+  int quiet = 0, sweep = 0;
   bool converged = false;
-  for (int sweep = 0; sweep < kJ32MaxSweeps && !converged; ++sweep) {
+  for (; sweep < kJ32MaxSweeps && !converged; ++sweep) {
     for (int r = 0; r < N - 1; ++r) {
       if (tid == 0) sh_active = 0;
       __syncthreads();
@@ -269,6 +269,7 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
     const int i = e % n, j = e / n;
     s.F32b[i + n * j] = V[i + lda * j];
   }
+  if (tid == 0) s.eig_sweeps32 += sweep;
 }
 
 int jacobi32_smem_bytes(int n) {

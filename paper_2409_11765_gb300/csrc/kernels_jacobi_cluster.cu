@@ -7,9 +7,12 @@
 //     owns slots [c spc, (c+1) spc) and keeps the full columns of A and of the
 //     eigenvector accumulator V for the players sitting in its slots. One warp
 //     serves one slot.
-//   * Each step: every warp computes its pair's rotation from its own two
-//     columns and writes it into the rotation table of every CTA of the
-//     cluster (distributed shared memory). After a cluster barrier each warp
+//   * Each step: lane j of warp 0 computes the rotation of local slot j from
+//     the slot's two columns (one lane per pair keeps the FP64 work of the
+//     rotations to one warp instruction stream per CTA) and writes it into the
+//     rotation table of every CTA of the cluster (distributed shared memory);
+//     p, q and the rotate flag travel packed in one word. After a cluster
+//     barrier each warp
 //     applies A <- A J and V <- V J to its two columns (column mixing), then
 //     A <- J^T A to the rows p_i, q_i of its two columns for every rotated pair
 //     (row mixing), then sets its pair's 2 x 2 diagonal block exactly
@@ -41,8 +44,8 @@ namespace {
 struct CLayout {
   int stride, nbuf, spc, P, N, threads;
   size_t bytes;
-  size_t colA, colV, rc, rs, evall;     // double arrays
-  size_t ids, rp, rq, ra, map;          // int arrays
+  size_t colA, colV, rc, rs, rt, evall;  // double arrays
+  size_t ids, rpq, map;                  // int arrays
 };
 
 __host__ __device__ inline CLayout make_layout(int max_n) {
@@ -58,12 +61,11 @@ __host__ __device__ inline CLayout make_layout(int max_n) {
   L.colV = d; d += static_cast<size_t>(L.nbuf) * L.stride;
   L.rc = d; d += L.P;
   L.rs = d; d += L.P;
+  L.rt = d; d += L.P;
   L.evall = d; d += L.N;
   size_t i = 0;
   L.ids = i; i += L.nbuf;
-  L.rp = i; i += L.P;
-  L.rq = i; i += L.P;
-  L.ra = i; i += L.P;
+  L.rpq = i; i += L.P;
   L.map = i; i += 4 * L.spc;  // two parities x (top, bottom) buffer of each local slot
   L.bytes = d * 8 + i * 4 + 16;
   return L;
@@ -89,12 +91,11 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
   double* colV = dsm + L.colV;
   double* rc = dsm + L.rc;
   double* rs = dsm + L.rs;
+  double* rt = dsm + L.rt;
   double* evall = dsm + L.evall;
   int* ibase = reinterpret_cast<int*>(dsm + (L.evall + L.N));
   int* ids = ibase + L.ids;
-  int* rp = ibase + L.rp;
-  int* rq = ibase + L.rq;
-  int* ra = ibase + L.ra;
+  int* rpq = ibase + L.rpq;  // p | q << 12 | rotate << 24 (n <= 256)
   int* map = ibase + L.map;  // map[par * 2 spc + 2 k] = top buffer, +1 = bottom buffer
 
   const int n = s.n, ldn = s.ldn;
@@ -132,57 +133,58 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
   for (; sweeps < kCMaxSweeps && !converged; ++sweeps) {
     for (int step = 0; step < N - 1; ++step) {
       const int* mp = map + par * 2 * spc;
-      int bt = 0, bb = 0;
-      double c = 1.0, sn = 0.0, tn = 0.0, app = 0.0, aqq = 0.0, apq = 0.0;
-      int p = 0, q = 0, act = 0;
-      if (mine) {
-        bt = mp[2 * k];
-        bb = mp[2 * k + 1];
-        p = ids[bt];
-        q = ids[bb];
+      if (warp == 0 && lane < nloc) {  // rotation of local slot `lane`
+        const int ft = mp[2 * lane], fb = mp[2 * lane + 1];
+        const int p = ids[ft], q = ids[fb];
+        double c = 1.0, sn = 0.0, tn = 0.0;
+        int act = 0;
         if (p < n && q < n) {
-          app = colA[bt * st + p];
-          aqq = colA[bb * st + q];
-          apq = colA[bb * st + p];
-          if (apq != 0.0 && fabs(apq) > kCTol * sqrt(fabs(app * aqq))) {
-            const double theta = (aqq - app) / (2.0 * apq);
-            const double at = fabs(theta);
-            tn = (at > 1e150) ? 0.5 / theta : (theta >= 0.0 ? 1.0 : -1.0) / (at + sqrt(theta * theta + 1.0));
-            c = 1.0 / sqrt(tn * tn + 1.0);
-            sn = tn * c;
+          const double app = colA[ft * st + p], aqq = colA[fb * st + q], apq = colA[fb * st + p];
+          if (jacobi_rotates(app, aqq, apq, kCTol * kCTol)) {
+            jacobi_rotation(app, aqq, apq, tn, c, sn);
             act = 1;
           }
         }
-        // publish the rotation in every CTA's table (lanes 0..7 write one CTA each)
-        if (lane < kCS) {
-          const int gi = g0 + k;
-          cl.map_shared_rank(rc, lane)[gi] = c;
-          cl.map_shared_rank(rs, lane)[gi] = sn;
-          cl.map_shared_rank(rp, lane)[gi] = p;
-          cl.map_shared_rank(rq, lane)[gi] = q;
-          cl.map_shared_rank(ra, lane)[gi] = act;
+        const int gi = g0 + lane;
+        const int pq = p | (q << 12) | (act << 24);
+        rt[gi] = tn;
+#pragma unroll
+        for (int cc = 0; cc < kCS; ++cc) {
+          cl.map_shared_rank(rc, cc)[gi] = c;
+          cl.map_shared_rank(rs, cc)[gi] = sn;
+          cl.map_shared_rank(rpq, cc)[gi] = pq;
         }
       }
       cl.sync();  // rotation table complete everywhere
-      int any = 0;
-      for (int i = lane; i < P; i += 32) any |= ra[i];
-      any = __any_sync(0xffffffffu, any);
-      if (tid == 0 && crank == 0) {
-        int cnt = 0;
-        for (int i = 0; i < P; ++i) cnt += ra[i];
-        rotations += cnt;
-      }
-      quiet = any ? 0 : quiet + 1;
+      int cnt = 0;
+      for (int i = lane; i < P; i += 32) cnt += rpq[i] >> 24;
+      cnt = __reduce_add_sync(0xffffffffu, cnt);
+      if (tid == 0 && crank == 0) rotations += cnt;
+      quiet = cnt ? 0 : quiet + 1;
       if (quiet >= N - 1) {
         converged = true;
         break;  // uniform: every warp of the cluster saw the same table
       }
-      if (mine && any) {
+      int bt = 0, bb = 0;
+      if (mine) {
+        bt = mp[2 * k];
+        bb = mp[2 * k + 1];
+      }
+      if (mine && cnt) {
+        const int gi = g0 + k;
+        const int pq = rpq[gi];
+        const int act = pq >> 24, p = pq & 0xfff, q = (pq >> 12) & 0xfff;
         double* At = colA + bt * st;
         double* Ab = colA + bb * st;
+        double app = 0.0, aqq = 0.0, apq = 0.0;
         if (act) {  // A <- A J and V <- V J on the pair's columns
+          app = At[p];
+          aqq = Ab[q];
+          apq = Ab[p];
+          const double c = rc[gi], sn = rs[gi];
           double* Vt = colV + bt * st;
           double* Vb = colV + bb * st;
+          __syncwarp();  // the block entries are read before any lane overwrites them
           for (int r = lane; r < n; r += 32) {
             const double x = At[r], y = Ab[r];
             At[r] = c * x - sn * y;
@@ -195,8 +197,9 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
         }
         // A <- J^T A: rows p_i, q_i of both columns, every rotated pair
         for (int i = lane; i < P; i += 32) {
-          if (!ra[i]) continue;
-          const int pi = rp[i], qi = rq[i];
+          const int pqi = rpq[i];
+          if (!(pqi >> 24)) continue;
+          const int pi = pqi & 0xfff, qi = (pqi >> 12) & 0xfff;
           const double ci = rc[i], si = rs[i];
           double x = At[pi], y = At[qi];
           At[pi] = ci * x - si * y;
@@ -208,6 +211,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
         }
         __syncwarp();
         if (act && lane == 0) {  // exact 2 x 2 diagonal block
+          const double tn = rt[gi];
           At[p] = app - tn * apq;
           Ab[q] = aqq + tn * apq;
           At[q] = 0.0;
