@@ -109,7 +109,6 @@ template <bool SMEM>
 __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_n, int hi_n) {
   extern __shared__ double dsm[];
   __shared__ double shr[32];
-  __shared__ int sh_active;
   __shared__ long long sh_rot;
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due) return;
@@ -163,9 +162,9 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
       V[i + lda * j] = s.B[i + static_cast<long long>(ldn) * j];
     }
   }
+  if (tid == 0) sh_rot = 0;
   __syncthreads();
 
-  if (tid == 0) sh_rot = 0;
   int sweeps = 0;
   // every pair meets once in any N - 1 consecutive steps, so N - 1 steps in a
   // row without a rotation mean convergence (same result as a quiet sweep)
@@ -173,9 +172,8 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   bool converged = false;
   for (; sweeps < kJacobiMaxSweeps && !converged; ++sweeps) {
     for (int r = 0; r < N - 1; ++r) {
-      if (tid == 0) sh_active = 0;
-      __syncthreads();
       // rotations of this step
+      int act_any = 0;
       for (int i = tid; i < P; i += kJacobiNT) {
         int p, q;
         rr_pair(r, i, N, p, q);
@@ -195,16 +193,30 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         rq[i] = q;
         ra[i] = act;
         if (act) {
-          sh_active = 1;
+          act_any = 1;
           atomicAdd(reinterpret_cast<unsigned long long*>(&sh_rot), 1ull);
         }
       }
-      __syncthreads();
-      quiet = sh_active ? 0 : quiet + 1;
-      if (quiet >= N - 1) {
-        converged = true;
-        break;  // uniform over the block (sh_active read after the barrier)
+      if (__syncthreads_count(act_any) == 0) {
+        // a quiet step: if no off-diagonal entry passes the test any more, the
+        // rest of the quiet window would change nothing
+        ++quiet;
+        if (quiet == 1 || quiet % (SMEM ? 16 : 256) == 0) {
+          int pend = 0;
+          for (int j = tid >> 5; j < n && !pend; j += kJacobiNT / 32) {
+            const double ajj = A[j + lda * j];
+            for (int i = tid & 31; i < j; i += 32)
+              pend |= jacobi_rotates(A[i + lda * i], ajj, A[i + lda * j], kJacobiTol * kJacobiTol);
+          }
+          if (!__syncthreads_or(pend)) quiet = N - 1;
+        }
+        if (quiet >= N - 1) {
+          converged = true;
+          break;  // uniform over the block: the counts come from block barriers
+        }
+        continue;
       }
+      quiet = 0;
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;
       for (int b = tid; b < nblk; b += kJacobiNT) {

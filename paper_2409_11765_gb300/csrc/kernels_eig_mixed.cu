@@ -23,7 +23,7 @@
 namespace cmaes_gb300 {
 
 constexpr int kE32Max = 160;            // FP32 Jacobi keeps A32 and V32 in shared memory
-constexpr int kJ32NT = 512;
+constexpr int kJ32NT = 1024;
 constexpr float kJ32Tol = 1e-6f;
 constexpr int kJ32MaxSweeps = 20;
 
@@ -150,22 +150,31 @@ __global__ void __launch_bounds__(256) k_eig_copy_b(Search* S, TileMap tm) {
 // FP32 cyclic Jacobi on A32 (F32a, symmetrised on load) with V32 = I; V32 is
 // written to F32b. Rotations below FP32 resolution are skipped: a pair turns
 // only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
-__global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
+// FP32 arithmetic is cheap here, so a step costs its instruction count: the
+// rotation table is packed (p | q << 10 | rotate << 20, (c, s) as float2),
+// the upper-triangle 2 x 2 blocks come from a table built once, V <- V J runs
+// one warp per pair over the rows, and the rotation count of a step is the
+// barrier's own count.
+__device__ __forceinline__ bool j32_rotates(float app, float aqq, float apq, float floor_abs) {
+  return fabsf(apq) > floor_abs && fabsf(apq) > kJ32Tol * sqrtf(fabsf(app * aqq));
+}
+
+__global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   extern __shared__ float fsm[];
-  __shared__ int sh_active;
   __shared__ float sh_amax;
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due || !s.mixed || s.n > kE32Max || s.n <= 32) return;
+  constexpr int NW = kJ32NT / 32;
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
+  const int lane = tid & 31, warp = tid >> 5;
   const int lda = N + 1;
+  const int nblk = P * (P + 1) / 2;
   float* A = fsm;
   float* V = A + lda * N;
-  float* rc = V + lda * N;
-  float* rsn = rc + P;
-  float* rtn = rsn + P;
-  int* rp = reinterpret_cast<int*>(rtn + P);
-  int* rq = rp + P;
-  int* ra = rq + P;
+  float2* rcs = reinterpret_cast<float2*>(V + lda * N);  // N lda even: 8-byte aligned
+  float* rt = reinterpret_cast<float*>(rcs + P);
+  int* rpq = reinterpret_cast<int*>(rt + P);
+  int* blk = rpq + P;  // block b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi: Pi | Qi << 16
   for (int e = tid; e < N * N; e += kJ32NT) {
     const int i = e % N, j = e / N;
     float a = 0.f;
@@ -173,30 +182,32 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
     A[i + lda * j] = a;
     V[i + lda * j] = (i == j && i < n) ? 1.f : 0.f;
   }
+  for (int Qi = warp; Qi < P; Qi += NW)
+    for (int Pi = lane; Pi <= Qi; Pi += 32) blk[Qi * (Qi + 1) / 2 + Pi] = Pi | (Qi << 16);
   __syncthreads();
-  if (tid == 0) {
+  if (warp == 0) {
     float m = 0.f;
-    for (int i = 0; i < n; ++i) m = fmaxf(m, fabsf(A[i + lda * i]));
-    sh_amax = m;
+    for (int i = lane; i < n; i += 32) m = fmaxf(m, fabsf(A[i + lda * i]));
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    if (lane == 0) sh_amax = m;
   }
   __syncthreads();
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
+  const int M = N - 1;
   int quiet = 0, sweep = 0;
   bool converged = false;
   for (; sweep < kJ32MaxSweeps && !converged; ++sweep) {
-    for (int r = 0; r < N - 1; ++r) {
-      if (tid == 0) sh_active = 0;
-      __syncthreads();
-      for (int i = tid; i < P; i += kJ32NT) {
-        const int M = N - 1;
-        const int p = (i == 0) ? r : (r + i) % M;
-        const int q = (i == 0) ? M : (r - i + M) % M;
+    for (int r = 0; r < M; ++r) {
+      int act = 0;
+      if (tid < P) {  // round-robin pair tid of step r (player N - 1 fixed)
+        const int p = (tid == 0) ? r : (r + tid) % M;
+        const int q = (tid == 0) ? M : (r - tid + M) % M;
         float c = 1.f, sn = 0.f, tn = 0.f;
-        int act = 0;
         if (p < n && q < n) {
           const float app = A[p + lda * p], aqq = A[q + lda * q], apq = A[p + lda * q];
-          if (fabsf(apq) > floor_abs && fabsf(apq) > kJ32Tol * sqrtf(fabsf(app * aqq))) {
+          if (j32_rotates(app, aqq, apq, floor_abs)) {
             const float theta = (aqq - app) / (2.f * apq);
             const float at = fabsf(theta);
             tn = (at > 1e18f) ? 0.5f / theta : (theta >= 0.f ? 1.f : -1.f) / (at + sqrtf(theta * theta + 1.f));
@@ -205,40 +216,49 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
             act = 1;
           }
         }
-        rc[i] = c;
-        rsn[i] = sn;
-        rtn[i] = tn;
-        rp[i] = p;
-        rq[i] = q;
-        ra[i] = act;
-        if (act) sh_active = 1;
+        rcs[tid] = make_float2(c, sn);
+        rt[tid] = tn;
+        rpq[tid] = p | (q << 10) | (act << 20);
       }
-      __syncthreads();
-      quiet = sh_active ? 0 : quiet + 1;
-      if (quiet >= N - 1) {
-        converged = true;
-        break;
+      const int nact = __syncthreads_count(act);
+      if (nact == 0) {
+        // a quiet step: if no off-diagonal entry passes the test any more, the
+        // remaining quiet steps of the window would change nothing
+        ++quiet;
+        if (quiet == 1 || (quiet & 15) == 0) {
+          int pend = 0;
+          for (int Qi = warp; Qi < n && !pend; Qi += NW) {
+            const float aqq = A[Qi + lda * Qi];
+            for (int Pi = lane; Pi < Qi; Pi += 32)
+              pend |= j32_rotates(A[Pi + lda * Pi], aqq, A[Pi + lda * Qi], floor_abs);
+          }
+          if (!__syncthreads_or(pend)) quiet = M;
+        }
+        if (quiet >= M) {
+          converged = true;
+          break;  // uniform: the counts come from block barriers
+        }
+        continue;
       }
-      // 2 x 2 block updates of A (blocks P <= Q, mirrored) and V <- V J
-      const int nblk = P * (P + 1) / 2;
+      quiet = 0;
+      // A <- J^T A J per 2 x 2 block (pair Pi rows, pair Qi columns, Pi <= Qi), mirrored
       for (int b = tid; b < nblk; b += kJ32NT) {
-        int bp = static_cast<int>((sqrtf(static_cast<float>(8 * b + 1)) - 1.0f) * 0.5f);
-        while ((bp + 1) * (bp + 2) / 2 <= b) ++bp;
-        while (bp * (bp + 1) / 2 > b) --bp;
-        const int Pi = b - bp * (bp + 1) / 2, Qi = bp;
-        const int aP = ra[Pi], aQ = ra[Qi];
-        if (!aP && !aQ) continue;
-        const int p1 = rp[Pi], q1 = rq[Pi], p2 = rp[Qi], q2 = rq[Qi];
+        const int pq = blk[b];
+        const int Pi = pq & 0xffff, Qi = pq >> 16;
+        const int wP = rpq[Pi], wQ = rpq[Qi];
+        if (!((wP | wQ) >> 20)) continue;
+        const int p1 = wP & 0x3ff, q1 = (wP >> 10) & 0x3ff, p2 = wQ & 0x3ff, q2 = (wQ >> 10) & 0x3ff;
         if (Pi == Qi) {
           const float app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
-          const float tt = rtn[Pi];
+          const float tt = rt[Pi];
           A[p1 + lda * p1] = app - tt * apq;
           A[q1 + lda * q1] = aqq + tt * apq;
           A[p1 + lda * q1] = 0.f;
           A[q1 + lda * p1] = 0.f;
           continue;
         }
-        const float cP = rc[Pi], sP = rsn[Pi], cQ = rc[Qi], sQ = rsn[Qi];
+        const float2 csP = rcs[Pi], csQ = rcs[Qi];
+        const float cP = csP.x, sP = csP.y, cQ = csQ.x, sQ = csQ.y;
         const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
         const float a = (vp1 && vp2) ? A[p1 + lda * p2] : 0.f;
         const float bb = (vp1 && vq2) ? A[p1 + lda * q2] : 0.f;
@@ -253,14 +273,19 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
         if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
         if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
       }
-      for (int e = tid; e < P * n; e += kJ32NT) {
-        const int pi = e / n, row = e % n;
-        if (!ra[pi]) continue;
-        const int p = rp[pi], q = rq[pi];
-        const float c = rc[pi], sn = rsn[pi];
-        const float vp = V[row + lda * p], vq = V[row + lda * q];
-        V[row + lda * p] = c * vp - sn * vq;
-        V[row + lda * q] = sn * vp + c * vq;
+      // V <- V J: one warp per rotated pair, lanes over the rows
+      for (int pi = warp; pi < P; pi += NW) {
+        const int w = rpq[pi];
+        if (!(w >> 20)) continue;
+        const int p = w & 0x3ff, q = (w >> 10) & 0x3ff;
+        const float2 cs = rcs[pi];
+        float* vp = V + lda * p;
+        float* vq = V + lda * q;
+        for (int row = lane; row < n; row += 32) {
+          const float x = vp[row], y = vq[row];
+          vp[row] = cs.x * x - cs.y * y;
+          vq[row] = cs.y * x + cs.x * y;
+        }
       }
       __syncthreads();
     }
@@ -274,7 +299,7 @@ __global__ void __launch_bounds__(kJ32NT) k_jacobi32(Search* S, int s0) {
 
 int jacobi32_smem_bytes(int n) {
   const int N = n + (n & 1), P = N / 2;
-  return 2 * (N + 1) * N * 4 + P * (3 * 4 + 3 * 4) + 16;
+  return 2 * (N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
 }
 
 void launch_eig_mixed(Search* S, TileMap tm32, int s0, int s1, int max_n, cudaStream_t st) {

@@ -80,6 +80,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
     k_jacobi_cluster(Search* S, int s0, int lo_n, int hi_n, int layout_n) {
   extern __shared__ double dsm[];
   __shared__ double shr[32];
+  __shared__ int shf[kCS];  // convergence verdict of each CTA of the cluster
   cg::cluster_group cl = cg::this_cluster();
   const int crank = static_cast<int>(cl.block_rank());
   Search& s = S[s0 + static_cast<int>(blockIdx.x) / kCS];
@@ -160,10 +161,43 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
       for (int i = lane; i < P; i += 32) cnt += rpq[i] >> 24;
       cnt = __reduce_add_sync(0xffffffffu, cnt);
       if (tid == 0 && crank == 0) rotations += cnt;
-      quiet = cnt ? 0 : quiet + 1;
+      if (cnt) {
+        quiet = 0;
+      } else if (++quiet == 1 || (quiet & 15) == 0) {
+        // a quiet step: if no off-diagonal entry passes the test any more, the
+        // rest of the quiet window would change nothing. Diagonal entries go to
+        // every CTA, each warp tests the upper part of its two columns, and the
+        // verdicts meet in every CTA's flag slots.
+        if (mine && lane < kCS) {
+          const int ft = mp[2 * k], fb = mp[2 * k + 1];
+          const int p = ids[ft], q = ids[fb];
+          double* ev = cl.map_shared_rank(evall, lane);
+          if (p < n) ev[p] = colA[ft * st + p];
+          if (q < n) ev[q] = colA[fb * st + q];
+        }
+        cl.sync();
+        int pend = 0;
+        if (mine) {
+          for (int h = 0; h < 2; ++h) {
+            const int buf = mp[2 * k + h];
+            const int id = ids[buf];
+            if (id >= n) continue;
+            const double ajj = evall[id];
+            const double* col = colA + buf * st;
+            for (int r = lane; r < id; r += 32) pend |= jacobi_rotates(evall[r], ajj, col[r], kCTol * kCTol);
+          }
+        }
+        pend = __syncthreads_or(pend);
+        if (tid < kCS) cl.map_shared_rank(shf, tid)[crank] = pend;
+        cl.sync();
+        int open = 0;
+#pragma unroll
+        for (int c = 0; c < kCS; ++c) open |= shf[c];
+        if (!open) quiet = N - 1;
+      }
       if (quiet >= N - 1) {
         converged = true;
-        break;  // uniform: every warp of the cluster saw the same table
+        break;  // uniform: every warp of the cluster saw the same table and flags
       }
       int bt = 0, bb = 0;
       if (mine) {
