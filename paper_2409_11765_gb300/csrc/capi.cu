@@ -219,13 +219,11 @@ static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
 
 static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap sq = h->tiles(TK_SQUARE, s0, s1);
-  if (h->mixed) {
-    TileMap t32 = h->tiles(TK_SQUARE32, s0, s1);
-    launch_eig_mixed(h->dS, t32, s0, s1, h->max_n, st);
-    if (t32.total > 0) {
-      h->launches += 11;
-      h->phase_launch[kPhaseEig] += 11;
-    }
+  {
+    TileMap tfl = h->tiles(TK_FLAT, s0, s1);
+    const int nl = launch_eig_mixed(h->dS, tfl, s0, s1, h->max_n, st);
+    h->launches += nl;
+    h->phase_launch[kPhaseEig] += nl;
   }
   launch_eig_gemm_CB(h->dS, sq, st);
   count_launch(h, kPhaseEig, sq.total);
@@ -440,13 +438,13 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += align256(static_cast<size_t>(ceil_div(n, 256)) * 8);
       b += align256(n_ * 4);                             // lam32
       b += align256(static_cast<size_t>(x.mu_cap) * 4);  // w32
-      if (n <= eig_mixed_max_n()) b += 2 * align256(n_ * n_ * 4);  // F32a F32b
       b += align256(ldn * lc * 8);                     // X
     } else {
       if (x.cov_nch > 1) b += align256(static_cast<size_t>(tiles_sym(n)) * x.cov_nch * 4096 * 8);
       b += 4 * align256(ldn * lc * 8);                 // Z Y X U
     }
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
+    if (eig_refined_route(n)) b += align256(n_ * n_ * 4) + 3 * align256(ldn * n_ * 8);  // F32b EX EG EH
     b += align256(lc * 8);                             // f
     b += 2 * align256(lc * 4);                         // order rank
     base[s] = total;
@@ -506,10 +504,6 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(ceil_div(x.n, 256)) * 8));
       x.lam32 = reinterpret_cast<float*>(take(n_ * 4));
       x.w32 = reinterpret_cast<float*>(take(static_cast<size_t>(x.mu_cap) * 4));
-      if (x.n <= eig_mixed_max_n()) {
-        x.F32a = reinterpret_cast<float*>(take(n_ * n_ * 4));
-        x.F32b = reinterpret_cast<float*>(take(n_ * n_ * 4));
-      }
     } else {
       x.covpart = x.cov_nch > 1
                       ? reinterpret_cast<double*>(take(static_cast<size_t>(tiles_sym(x.n)) * x.cov_nch * 4096 * 8))
@@ -521,6 +515,12 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.Q = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.EA = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.ET = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    if (eig_refined_route(x.n)) {
+      x.F32b = reinterpret_cast<float*>(take(n_ * n_ * 4));
+      x.EX = reinterpret_cast<double*>(take(ldn * n_ * 8));
+      x.EG = reinterpret_cast<double*>(take(ldn * n_ * 8));
+      x.EH = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    }
     if (h->mixed) {
       x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
     } else {
@@ -563,7 +563,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TCOBJ: t = h->mixed ? tiles_tc_objective(x.lam_cap) : 0; break;
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
         case TK_TCSYM: t = h->mixed ? 16 * tiles_tc_sym(x.n) : 0; break;  // reduce: 16 blocks per tile
-        case TK_SQUARE32: t = (h->mixed && x.n > 32 && x.n <= eig_mixed_max_n()) ? tiles_square32(x.n) : 0; break;
+        case TK_FLAT: t = eig_refined_route(x.n) ? tiles_flat(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

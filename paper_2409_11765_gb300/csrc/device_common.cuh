@@ -258,4 +258,9 @@ __device__ __forceinline__ bool jacobi_rotates(double app, double aqq, double ap
   return apq != 0.0 && apq * apq > tol2 * fabs(app * aqq);
 }
 
+// The same test with an absolute floor: entries at or below `floor` never turn.
+__device__ __forceinline__ bool jacobi_rotates(double app, double aqq, double apq, double tol2, double floor) {
+  return fabs(apq) > floor && apq * apq > tol2 * fabs(app * aqq);
+}
+
 }  // namespace cmaes_gb300

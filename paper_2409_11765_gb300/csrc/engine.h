@@ -62,7 +62,8 @@ struct Search {
   float *Y32;         // kp x lam_cap, y = B D z from the FP32 accumulators
   double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation
   double fbest64;     // FP64 value of this generation's best point
-  float *F32a, *F32b; // n x n FP32 scratch of the mixed-precision eigensolver route
+  float *F32b;        // n x n FP32 scratch of the refined eigensolver route (V32)
+  double *EX, *EG, *EH;  // ldn x n FP64 scratch of its refinement steps (with EA, ET)
   int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
@@ -92,7 +93,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_SQUARE32, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -119,6 +120,11 @@ void launch_eig_gemm_BtT(Search* S, TileMap tm, cudaStream_t st);
 // n <= kJacobiClusterN), one CTA per search on global memory (larger n).
 constexpr int kJacobiSmallN = 32;
 constexpr int kJacobiClusterN = 256;
+// Searches with kJacobiSmallN < n <= kEigMixedMaxN (any precision) take the
+// FP32-preconditioned, FP64-refined route of kernels_eig_mixed.cu.
+constexpr int kEigMixedMaxN = 160;
+__host__ __device__ inline bool eig_refined_route(int n) { return n > kJacobiSmallN && n <= kEigMixedMaxN; }
+__host__ __device__ inline bool eig_refined_route(const Search& s) { return eig_refined_route(s.n); }
 void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int lo_n, int hi_n, int max_n,
                            cudaStream_t st);
 void launch_jacobi_cluster(Search* S, int s0, int s1, int lo_n, int hi_n, int layout_n, cudaStream_t st);
@@ -142,9 +148,8 @@ void launch_tc_cov_reduce(Search* S, TileMap tm, cudaStream_t st);
 void launch_reeval(Search* S, TileMap tm, cudaStream_t st);
 // mixed-precision eigensolver route (kernels_eig_mixed.cu): FP32 Jacobi
 // sweeps, Newton-Schulz lift to FP64, then the FP64 Jacobi finishes
-int eig_mixed_max_n();
-int tiles_square32(int n);
-void launch_eig_mixed(Search* S, TileMap tm32, int s0, int s1, int max_n, cudaStream_t st);
+int tiles_flat(int n);
+int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);

@@ -46,9 +46,9 @@ int jacobi_smem_max_n() {
   return best;
 }
 
-// Searches whose warm start is prepared by the mixed-precision route
+// Searches whose warm start is prepared by the refined route
 // (kernels_eig_mixed.cu) skip the FP64 B^T C B below.
-__device__ __forceinline__ bool mixed_route(const Search& s) { return s.mixed && s.n > 32 && s.n <= 160; }
+__device__ __forceinline__ bool mixed_route(const Search& s) { return eig_refined_route(s); }
 
 // ET = C B (square tiles; only searches whose decomposition is due).
 __global__ void __launch_bounds__(256) k_eig_gemm_CB(Search* S, TileMap tm) {

@@ -1,154 +1,286 @@
-// kernels_eig_mixed.cu -- mixed-precision preconditioning of the warm-started
-// Jacobi eigendecomposition (mixed-precision handles only).
+// kernels_eig_mixed.cu -- mixed-precision route of the warm-started
+// eigendecomposition (32 < n <= 160, every handle precision: the FP32 work
+// only supplies the starting basis, the result is FP64-accurate).
 //
 // The FP64 Jacobi of kernels_eig.cu / kernels_jacobi_cluster.cu needs about
 // seven sweeps per decomposition when C moves a lot between generations, and on
-// GB300 every sweep is bound by the FP64 pipe. Here most of those sweeps run in
-// FP32 (a 64x faster pipe) and the FP64 Jacobi only finishes the job:
-//   1. A32 = B^T C B in FP32 (the warm start, from the previous basis B).
-//   2. FP32 cyclic Jacobi on A32 (same round-robin ordering and rotation
-//      formula) until the off-diagonal reaches FP32 resolution; V32 collects
-//      the rotations (V32 ~ the eigenvectors of A32, orthonormal to ~1e-6).
-//   3. W = B V32 in FP64, made orthonormal to FP64 precision by two
-//      Newton-Schulz steps W <- W (3 I - W^T W) / 2 (error e -> 1.5 e^2).
-//   4. A = W^T C W in FP64 (nearly diagonal), B <- W; the FP64 Jacobi then
-//      runs on (A, B) exactly as in the FP64 path and delivers the FP64
-//      eigenvalues, eigenvectors and canonical form.
-// Every product here is a small dense GEMM on CUDA cores (32 x 32 tiles so that
-// n = 100 still spreads over many SMs); the tensor cores are not used because
-// step 3 and 4 need FP64 and step 1 feeds a FP32-accurate Jacobi.
+// GB300 every sweep is bound by the FP64 pipe (1/64 of the FP32 rate) and by
+// the latency of its steps. Here the sweeps run in FP32 and FP64 accuracy is
+// recovered by dense FP64 products that spread over every SM:
+//   1. A = B^T C B in FP64 (the warm start, from the previous basis B), and
+//      A32 = A - c I in FP32 with c = trace(A) / n.
+//   2. FP32 cyclic Jacobi on A32 (round-robin ordering, the rotation of
+//      Golub & Van Loan §8.5) down to FP32 resolution; V32 collects the
+//      rotations. X0 = B V32 in FP64 is an orthonormal basis to ~1e-7 whose
+//      columns are eigenvectors of C to FP32 accuracy.
+//   3. Two steps of the iterative refinement of Ogita & Aishima ("Iterative
+//      refinement for symmetric eigenvalue decomposition", Japan J. Indust.
+//      Appl. Math. 35, 2018): with S = X^T C X, G = X^T X, lambda_i = s_ii / g_ii,
+//        e_ii = (1 - g_ii) / 2,
+//        e_ij = (s_ij - lambda_j g_ij) / (lambda_j - lambda_i)   (i != j),
+//        X <- X + X E,
+//      the first-order correction that makes X orthonormal and C-diagonal
+//      together; the error squares at every step. A pair whose correction
+//      would exceed 2^-10 (eigenvalues too close for first order) only gets the
+//      orthogonality part e_ij = -g_ij / 2 and is left to step 5.
+//   4. One Newton-Schulz step X <- X + X (I - X^T X) / 2 removes the
+//      second-order loss of orthogonality that large first-order corrections
+//      leave (error e -> 1.5 e^2).
+//   5. A = X^T C X in FP64, B <- X; the FP64 Jacobi then runs on (A, B) as in
+//      the FP64 path: it rotates what step 3 left (pairs of close eigenvalues),
+//      normally ends at its first quiet step, and delivers the eigenvalues, the
+//      PD guard and the canonical form. On mixed-precision handles the
+//      off-diagonal entries below n eps64 max|a_ii|, the rounding level of the
+//      product that formed A, are left alone; FP64 handles keep the plain
+//      relative test, so their result matches a full FP64 Jacobi.
+// Because X^T X is measured and corrected every decomposition, rounding does
+// not accumulate in B from one generation's warm start to the next.
+// Every FP64 product reads its left operand along its leading dimension
+// (each X is also stored transposed) and computes 384 consecutive outputs of
+// the n x n result per CTA, three per lane, over the full K.
 #include <cmath>
 #include "device_common.cuh"
 
 namespace cmaes_gb300 {
 
-constexpr int kE32Max = 160;            // FP32 Jacobi keeps A32 and V32 in shared memory
+constexpr int kE32Max = kEigMixedMaxN;  // FP32 Jacobi keeps A32 and V32 in shared memory
 constexpr int kJ32NT = 1024;
 constexpr float kJ32Tol = 1e-6f;
 constexpr int kJ32MaxSweeps = 20;
 
-int eig_mixed_max_n() { return kE32Max; }
-int tiles_square32(int n) { const int t = ceil_div(n, 32); return t * t; }
+__device__ __forceinline__ bool mixed_route_due(const Search& s) {
+  return !s.done && s.eig_due && eig_refined_route(s);
+}
 
-// 32 x 32 output tile, K step 32, 256 threads with 2 x 2 outputs each.
-template <typename T>
-struct Gemm32Smem {
-  T As[32][33];
-  T Bs[32][33];
+// ---------------------------------------------------------------------------
+// FP64 products of the refinement: CTA t of a search computes outputs
+// o = t * 384 + warp * 96 + lane + 32 u (u = 0, 1, 2) of the n x n result in
+// column-major order, each over the full K = n. The left operand is read along
+// its leading dimension (consecutive lanes, consecutive rows), the right one is
+// shared by the lanes of a column. FP64 issues at 1/64 of the FP32 rate, so
+// the three independent accumulators keep the pipe busy without staging the
+// operands in shared memory; they stay in L1 / L2 (n <= 160).
+// ---------------------------------------------------------------------------
+constexpr int kFW = 4;               // warps per CTA
+constexpr int kFP = 3;               // outputs per lane
+constexpr int kFO = kFW * 32 * kFP;  // outputs per CTA
+int tiles_flat(int n) { return ceil_div(n * n, kFO); }
+
+template <int NACC, class LA, class LB, class EPI>
+__device__ __forceinline__ void gemm_flat_f64(int n, int t, const LA& la, const LB& lb, const EPI& epi) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int base = t * kFO + warp * 32 * kFP + lane;
+  const int nn = n * n;
+  int ii[kFP], jj[kFP];
+#pragma unroll
+  for (int u = 0; u < kFP; ++u) {
+    const int o = base + 32 * u;
+    ii[u] = o < nn ? o % n : 0;  // lanes past the end compute (0, 0) and store nothing
+    jj[u] = o < nn ? o / n : 0;
+  }
+  double acc[NACC][kFP];
+#pragma unroll
+  for (int a = 0; a < NACC; ++a)
+#pragma unroll
+    for (int u = 0; u < kFP; ++u) acc[a][u] = 0.0;
+#pragma unroll 4
+  for (int k = 0; k < n; ++k) {
+#pragma unroll
+    for (int u = 0; u < kFP; ++u) {
+      const double x = la(ii[u], k);
+#pragma unroll
+      for (int a = 0; a < NACC; ++a) acc[a][u] = fma(x, lb(a, k, jj[u]), acc[a][u]);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < kFP; ++u)
+    if (base + 32 * u < nn) epi(ii[u], jj[u], acc[0][u], acc[NACC - 1][u]);
+}
+
+// Buffers of the refinement (ldn x n, FP64): EA, ET, EX, EG, EH plus B.
+enum OaOp {
+  OA_W0 = 0,  // (C B)^T                    -> EG   (warm start, C symmetric)
+  OA_W1,      // A = (C B)^T B = B^T C B    -> EH
+  OA_X0,      // X0 = B V32                 -> ET, X0^T -> EX
+  OA_T0,      // T0 = C X0 (ET)             -> EA
+  OA_SG0,     // S0 = X0^T T0, G0 = X0^T X0 -> EG, EH   (X0^T in EX)
+  OA_E0,      // E0 from (EG, EH)           -> EA
+  OA_U0,      // X1 = X0 + X0 E0            -> EG, X1^T -> EH
+  OA_T1,      // T1 = C X1 (EG)             -> EA
+  OA_SG1,     // S1, G1 (X1^T in EH)        -> ET, EX
+  OA_E1,      // E1 from (ET, EX)           -> EA
+  OA_U1,      // X2 = X1 + X1 E1            -> B, X2^T -> ET
+  OA_G2,      // M = (I - X2^T X2) / 2      -> EX
+  OA_N2,      // X3 = X2 + X2 M             -> EG, X3^T -> EH   (Newton-Schulz)
+  OA_T3,      // T3 = C X3 (EG)             -> EX
+  OA_A,       // A = X3^T T3                -> EA, and B <- X3
 };
 
-template <typename T, class LA, class LB, class EPI>
-__device__ __forceinline__ void gemm32_tile(int M, int N, int K, int i0, int j0, const LA& la, const LB& lb,
-                                            const EPI& epi, Gemm32Smem<T>& sm) {
-  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
-  T acc[2][2] = {{0, 0}, {0, 0}};
-  for (int k0 = 0; k0 < K; k0 += 32) {
-    for (int e = tid; e < 32 * 32; e += 256) {
-      const int a = e & 31, b = e >> 5;  // a fastest
-      sm.As[b][a] = (i0 + a < M && k0 + b < K) ? la(i0 + a, k0 + b) : T(0);
-      sm.Bs[a][b] = (k0 + a < K && j0 + b < N) ? lb(k0 + a, j0 + b) : T(0);
-    }
-    __syncthreads();
-#pragma unroll 8
-    for (int kk = 0; kk < 32; ++kk) {
-      const T a0 = sm.As[kk][tr], a1 = sm.As[kk][tr + 16];
-      const T b0 = sm.Bs[kk][tc], b1 = sm.Bs[kk][tc + 16];
-      acc[0][0] = fma(a0, b0, acc[0][0]);
-      acc[0][1] = fma(a0, b1, acc[0][1]);
-      acc[1][0] = fma(a1, b0, acc[1][0]);
-      acc[1][1] = fma(a1, b1, acc[1][1]);
-    }
-    __syncthreads();
-  }
-#pragma unroll
-  for (int r = 0; r < 2; ++r)
-#pragma unroll
-    for (int c = 0; c < 2; ++c) {
-      const int i = i0 + tr + 16 * r, j = j0 + tc + 16 * c;
-      if (i < M && j < N) epi(i, j, acc[r][c]);
-    }
-}
-
-enum EigOp { OP_CB32 = 0, OP_BTT32, OP_BV, OP_WTW, OP_WM, OP_CW, OP_WTT };
-
-// One stage of the preconditioning, over the searches whose decomposition is
-// due and that take the mixed route. Scratch: F32a, F32b (n x n floats, ld n),
-// ET and EA (FP64 n x n, ld ldn).
-__global__ void __launch_bounds__(256) k_eig_stage(Search* S, TileMap tm, int op) {
+__global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int op) {
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
-  if (s.done || !s.eig_due || !s.mixed || s.n > kE32Max || s.n <= 32) return;
-  const int n = s.n, ldn = s.ldn, T = ceil_div(n, 32);
-  const int i0 = (t % T) * 32, j0 = (t / T) * 32;
-  const long long L = ldn;
-  float* f32a = s.F32a;
-  float* f32b = s.F32b;
+  if (!mixed_route_due(s)) return;
+  const int n = s.n;
+  const long long L = s.ldn;
   const double* C = s.C;
-  double* B = s.B;
-  double* ET = s.ET;
-  double* EA = s.EA;
-  if (op == OP_CB32 || op == OP_BTT32) {
-    __shared__ Gemm32Smem<float> sm;
-    if (op == OP_CB32)  // F32b = C B
-      gemm32_tile<float>(n, n, n, i0, j0,
-                         [=] __device__(int i, int k) { return static_cast<float>(C[i + L * k]); },
-                         [=] __device__(int k, int j) { return static_cast<float>(B[k + L * j]); },
-                         [=] __device__(int i, int j, float v) { f32b[i + n * j] = v; }, sm);
-    else                // F32a = B^T F32b
-      gemm32_tile<float>(n, n, n, i0, j0,
-                         [=] __device__(int i, int k) { return static_cast<float>(B[k + L * i]); },
-                         [=] __device__(int k, int j) { return f32b[k + n * j]; },
-                         [=] __device__(int i, int j, float v) { f32a[i + n * j] = v; }, sm);
-    return;
-  }
-  __shared__ Gemm32Smem<double> sm;
   switch (op) {
-    case OP_BV:   // ET = B V32 (V32 in F32b)
-      gemm32_tile<double>(n, n, n, i0, j0, [=] __device__(int i, int k) { return B[i + L * k]; },
-                          [=] __device__(int k, int j) { return static_cast<double>(f32b[k + n * j]); },
-                          [=] __device__(int i, int j, double v) { ET[i + L * j] = v; }, sm);
+    case OA_W0: {
+      const double* B = s.B;
+      double* TT = s.EG;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return C[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return B[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) { TT[j + L * i] = v; });
       break;
-    case OP_WTW:  // EA = (3 I - W^T W) / 2 with W = ET
-      gemm32_tile<double>(n, n, n, i0, j0, [=] __device__(int i, int k) { return ET[k + L * i]; },
-                          [=] __device__(int k, int j) { return ET[k + L * j]; },
-                          [=] __device__(int i, int j, double v) { EA[i + L * j] = (i == j ? 1.5 : 0.0) - 0.5 * v; },
-                          sm);
+    }
+    case OA_W1: {
+      const double* TT = s.EG;
+      const double* B = s.B;
+      double* A = s.EH;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return TT[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return B[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) { A[i + L * j] = v; });
       break;
-    case OP_WM:   // B = W M (W = ET, M = EA); the Newton-Schulz step
-      gemm32_tile<double>(n, n, n, i0, j0, [=] __device__(int i, int k) { return ET[i + L * k]; },
-                          [=] __device__(int k, int j) { return EA[k + L * j]; },
-                          [=] __device__(int i, int j, double v) { B[i + L * j] = v; }, sm);
+    }
+    case OA_X0: {
+      const double* B = s.B;
+      const float* V = s.F32b;
+      double* X = s.ET;
+      double* XT = s.EX;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return B[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return static_cast<double>(V[k + n * j]); },
+                       [=] __device__(int i, int j, double v, double) {
+                         X[i + L * j] = v;
+                         XT[j + L * i] = v;
+                       });
       break;
-    case OP_CW:   // ET = C B
-      gemm32_tile<double>(n, n, n, i0, j0, [=] __device__(int i, int k) { return C[i + L * k]; },
-                          [=] __device__(int k, int j) { return B[k + L * j]; },
-                          [=] __device__(int i, int j, double v) { ET[i + L * j] = v; }, sm);
+    }
+    case OA_T0:
+    case OA_T1:
+    case OA_T3: {
+      const double* X = op == OA_T0 ? s.ET : s.EG;
+      double* T = op == OA_T3 ? s.EX : s.EA;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return C[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return X[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) { T[i + L * j] = v; });
       break;
-    case OP_WTT:  // EA = B^T ET
-      gemm32_tile<double>(n, n, n, i0, j0, [=] __device__(int i, int k) { return B[k + L * i]; },
-                          [=] __device__(int k, int j) { return ET[k + L * j]; },
-                          [=] __device__(int i, int j, double v) { EA[i + L * j] = v; }, sm);
+    }
+    case OA_SG0:
+    case OA_SG1: {
+      const double* XT = op == OA_SG0 ? s.EX : s.EH;
+      const double* X = op == OA_SG0 ? s.ET : s.EG;
+      const double* T = s.EA;
+      double* So = op == OA_SG0 ? s.EG : s.ET;
+      double* Go = op == OA_SG0 ? s.EH : s.EX;
+      double* lam = s.D;  // scratch until the Jacobi writes D
+      gemm_flat_f64<2>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+                       [=] __device__(int a, int k, int j) { return a == 0 ? T[k + L * j] : X[k + L * j]; },
+                       [=] __device__(int i, int j, double sv, double gv) {
+                         So[i + L * j] = sv;
+                         Go[i + L * j] = gv;
+                         if (i == j) lam[i] = sv / gv;
+                       });
       break;
+    }
+    case OA_U0:
+    case OA_U1: {
+      const double* X = op == OA_U0 ? s.ET : s.EG;
+      const double* E = s.EA;
+      double* Xo = op == OA_U0 ? s.EG : s.B;
+      double* XTo = op == OA_U0 ? s.EH : s.ET;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return X[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return E[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) {
+                         const double x = X[i + L * j] + v;
+                         Xo[i + L * j] = x;
+                         XTo[j + L * i] = x;
+                       });
+      break;
+    }
+    case OA_G2: {
+      const double* XT = s.ET;
+      const double* X = s.B;
+      double* M = s.EX;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return X[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) {
+                         M[i + L * j] = 0.5 * ((i == j ? 1.0 : 0.0) - v);
+                       });
+      break;
+    }
+    case OA_N2: {
+      const double* X = s.B;
+      const double* M = s.EX;
+      double* Xo = s.EG;
+      double* XTo = s.EH;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return X[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return M[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) {
+                         const double x = X[i + L * j] + v;
+                         Xo[i + L * j] = x;
+                         XTo[j + L * i] = x;
+                       });
+      break;
+    }
+    case OA_A: {
+      const double* XT = s.EH;
+      const double* X = s.EG;
+      const double* T = s.EX;
+      double* A = s.EA;
+      double* B = s.B;
+      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+                       [=] __device__(int, int k, int j) { return T[k + L * j]; },
+                       [=] __device__(int i, int j, double v, double) {
+                         A[i + L * j] = v;
+                         B[i + L * j] = X[i + L * j];
+                       });
+      break;
+    }
   }
 }
 
-// ET <- B (the second Newton-Schulz step starts from the first one's result).
-__global__ void __launch_bounds__(256) k_eig_copy_b(Search* S, TileMap tm) {
+// E of one refinement step from S, G and lambda (elementwise, same output
+// order as the products). A pair is corrected to first order only when both
+// of its corrections stay below 2^-10; otherwise both entries only get the
+// orthogonality half -g_ij / 2. The bound keeps the second-order loss of
+// orthogonality of a step, sum_k |e_ki e_kj| <= n 2^-20, small enough that the
+// second step and the Newton-Schulz step bring X^T X to I within rounding
+// (1.5 (n 2^-20)^4 << eps64 for n <= 160).
+constexpr double kOaSep = 0x1p-10;
+__global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int step) {
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
-  if (s.done || !s.eig_due || !s.mixed || s.n > kE32Max || s.n <= 32) return;
-  const int n = s.n, ldn = s.ldn, T = ceil_div(n, 32);
-  const int i0 = (t % T) * 32, j0 = (t / T) * 32;
-  for (int e = threadIdx.x; e < 32 * 32; e += 256) {
-    const int i = i0 + (e & 31), j = j0 + (e >> 5);
-    if (i < n && j < n) s.ET[i + static_cast<long long>(ldn) * j] = s.B[i + static_cast<long long>(ldn) * j];
+  if (!mixed_route_due(s)) return;
+  const int n = s.n;
+  const long long L = s.ldn;
+  const double* Sm = step == 0 ? s.EG : s.ET;
+  const double* Gm = step == 0 ? s.EH : s.EX;
+  const double* lam = s.D;  // lambda_i = s_ii / g_ii from the product's epilogue
+  double* E = s.EA;
+  const int base = t * kFO + threadIdx.x;
+#pragma unroll
+  for (int u = 0; u < kFP; ++u) {
+    const int o = base + kFW * 32 * u;
+    if (o >= n * n) break;
+    const int i = o % n, j = o / n;
+    const double gij = Gm[i + L * j];
+    double e;
+    if (i == j) {
+      e = 0.5 * (1.0 - gij);
+    } else {
+      // the test is symmetric in (i, j), so e_ij + e_ji = -g_ij in both branches
+      const double li = lam[i], lj = lam[j];
+      const double num = Sm[i + L * j] - lj * gij, num_t = Sm[j + L * i] - li * gij;
+      const double den = lj - li, lim = kOaSep * fabs(den);
+      e = (fabs(num) <= lim && fabs(num_t) <= lim) ? num / den : -0.5 * gij;
+    }
+    E[i + L * j] = e;
   }
 }
 
-// FP32 cyclic Jacobi on A32 (F32a, symmetrised on load) with V32 = I; V32 is
-// written to F32b. Rotations below FP32 resolution are skipped: a pair turns
+// FP32 cyclic Jacobi on A32 (from EH, symmetrised and shifted on load) with
+// V32 = I; V32 is written to F32b. Rotations below FP32 resolution are skipped: a pair turns
 // only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
 // FP32 arithmetic is cheap here, so a step costs its instruction count: the
 // rotation table is packed (p | q << 10 | rotate << 20, (c, s) as float2),
@@ -163,7 +295,7 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   extern __shared__ float fsm[];
   __shared__ float sh_amax;
   Search& s = S[s0 + blockIdx.x];
-  if (s.done || !s.eig_due || !s.mixed || s.n > kE32Max || s.n <= 32) return;
+  if (!mixed_route_due(s)) return;
   constexpr int NW = kJ32NT / 32;
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -175,10 +307,20 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   float* rt = reinterpret_cast<float*>(rcs + P);
   int* rpq = reinterpret_cast<int*>(rt + P);
   int* blk = rpq + P;  // block b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi: Pi | Qi << 16
+  // A32 = (B^T C B - c I) rounded to FP32, with c the mean eigenvalue (the
+  // trace over n, in FP64). The shift leaves the eigenvectors alone and lets
+  // FP32 resolve the spread of the spectrum around c, which is where nearly
+  // equal eigenvalues of an early descent (C close to a multiple of I) live.
+  const long long L = s.ldn;
+  const double* A64 = s.EH;
+  double tr = 0.0;
+  for (int i = tid; i < n; i += kJ32NT) tr += A64[i + L * i];
+  __shared__ double shs[kJ32NT / 32];
+  const double c = block_sum<kJ32NT>(tr, shs) / n;
   for (int e = tid; e < N * N; e += kJ32NT) {
     const int i = e % N, j = e / N;
     float a = 0.f;
-    if (i < n && j < n) a = 0.5f * (s.F32a[i + n * j] + s.F32a[j + n * i]);
+    if (i < n && j < n) a = static_cast<float>(0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0));
     A[i + lda * j] = a;
     V[i + lda * j] = (i == j && i < n) ? 1.f : 0.f;
   }
@@ -302,23 +444,33 @@ int jacobi32_smem_bytes(int n) {
   return 2 * (N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
 }
 
-void launch_eig_mixed(Search* S, TileMap tm32, int s0, int s1, int max_n, cudaStream_t st) {
-  if (tm32.total <= 0 || s1 <= s0) return;
-  const int g = tm32.total;
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_CB32);
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_BTT32);
+int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st) {
+  if (tflat.total <= 0 || s1 <= s0) return 0;
+  int nl = 0;
+  const int gf = tflat.total;
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_W0);
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_W1);
+  nl += 2;
   const int mn = max_n < kE32Max ? max_n : kE32Max;
   const int bytes = jacobi32_smem_bytes(mn);
   cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   k_jacobi32<<<s1 - s0, kJ32NT, bytes, st>>>(S, s0);
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_BV);    // ET = W = B V32
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_WTW);   // EA = (3I - W^T W)/2
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_WM);    // B = W EA
-  k_eig_copy_b<<<g, 256, 0, st>>>(S, tm32);          // ET = B
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_WTW);   // second Newton-Schulz step
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_WM);
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_CW);    // ET = C B
-  k_eig_stage<<<g, 256, 0, st>>>(S, tm32, OP_WTT);   // EA = B^T C B
+  ++nl;
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_X0);
+  ++nl;
+  for (int step = 0; step < 2; ++step) {
+    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_T0 : OA_T1);
+    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_SG0 : OA_SG1);
+    k_oa_e<<<gf, kFW * 32, 0, st>>>(S, tflat, step);
+    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_U0 : OA_U1);
+    nl += 4;
+  }
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_G2);
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_N2);
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_T3);
+  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_A);
+  nl += 4;
+  return nl;
 }
 
 }  // namespace cmaes_gb300

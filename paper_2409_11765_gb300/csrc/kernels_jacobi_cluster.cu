@@ -81,6 +81,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
   extern __shared__ double dsm[];
   __shared__ double shr[32];
   __shared__ int shf[kCS];  // convergence verdict of each CTA of the cluster
+  __shared__ double shm[kCS];  // max |a_ii| over each CTA's columns
   cg::cluster_group cl = cg::this_cluster();
   const int crank = static_cast<int>(cl.block_rank());
   Search& s = S[s0 + static_cast<int>(blockIdx.x) / kCS];
@@ -127,6 +128,31 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
     colV[b * st + r] = v;
   }
   __syncthreads();
+  // On the refined route A = X^T C X comes from FP64 products whose rounding
+  // reaches n eps64 max|a_ii| (the bound for a length-n dot product of the
+  // unit columns of X with those of C X); entries below that are noise and
+  // are not rotated: one such bound on FP64 handles (a rotation it skips moves
+  // an eigenvector by at most n eps64 / relative gap), four on mixed-precision
+  // handles, whose contract is a backward error of 1e-12. Elsewhere floor = 0:
+  // the plain relative test.
+  double floor_abs = 0.0;
+  if (eig_refined_route(s)) {
+    if (warp == 0) {
+      double m = 0.0;
+      for (int b = lane; b < 2 * nloc; b += 32) {
+        const int id = 2 * g0 + b;
+        if (id < n) m = fmax(m, fabs(colA[b * st + id]));
+      }
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+      if (lane < kCS) cl.map_shared_rank(shm, lane)[crank] = m;
+    }
+    cl.sync();
+    double amax = 0.0;
+#pragma unroll
+    for (int c = 0; c < kCS; ++c) amax = fmax(amax, shm[c]);
+    floor_abs = (s.mixed ? 4.0 : 1.0) * n * 0x1p-53 * amax;
+  }
 
   long long rotations = 0;
   int sweeps = 0, quiet = 0, par = 0;
@@ -141,7 +167,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
         int act = 0;
         if (p < n && q < n) {
           const double app = colA[ft * st + p], aqq = colA[fb * st + q], apq = colA[fb * st + p];
-          if (jacobi_rotates(app, aqq, apq, kCTol * kCTol)) {
+          if (jacobi_rotates(app, aqq, apq, kCTol * kCTol, floor_abs)) {
             jacobi_rotation(app, aqq, apq, tn, c, sn);
             act = 1;
           }
@@ -184,7 +210,8 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
             if (id >= n) continue;
             const double ajj = evall[id];
             const double* col = colA + buf * st;
-            for (int r = lane; r < id; r += 32) pend |= jacobi_rotates(evall[r], ajj, col[r], kCTol * kCTol);
+            for (int r = lane; r < id; r += 32)
+              pend |= jacobi_rotates(evall[r], ajj, col[r], kCTol * kCTol, floor_abs);
           }
         }
         pend = __syncthreads_or(pend);
