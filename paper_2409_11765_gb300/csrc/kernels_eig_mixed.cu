@@ -36,8 +36,8 @@
 // Because X^T X is measured and corrected every decomposition, rounding does
 // not accumulate in B from one generation's warm start to the next.
 // Every FP64 product reads its left operand along its leading dimension
-// (each X is also stored transposed) and computes 384 consecutive outputs of
-// the n x n result per CTA, three per lane, over the full K.
+// (each X is also stored transposed) and computes 256 consecutive outputs of
+// the n x n result per CTA, two per lane, over the full K.
 #include <cmath>
 #include "device_common.cuh"
 
@@ -54,16 +54,18 @@ __device__ __forceinline__ bool mixed_route_due(const Search& s) {
 
 // ---------------------------------------------------------------------------
 // FP64 products of the refinement: CTA t of a search computes outputs
-// o = t * 384 + warp * 96 + lane + 32 u (u = 0, 1, 2) of the n x n result in
+// o = t * 256 + warp * 64 + lane + 32 u (u = 0, 1) of the n x n result in
 // column-major order, each over the full K = n. The left operand is read along
 // its leading dimension (consecutive lanes, consecutive rows), the right one is
 // shared by the lanes of a column. FP64 issues at 1/64 of the FP32 rate, so
-// the three independent accumulators keep the pipe busy without staging the
-// operands in shared memory; they stay in L1 / L2 (n <= 160).
+// batches of loaded operands and independent accumulators keep the pipe busy
+// without staging the operands in shared memory; they stay in L1 / L2
+// (n <= 160).
 // ---------------------------------------------------------------------------
 constexpr int kFW = 4;               // warps per CTA
-constexpr int kFP = 3;               // outputs per lane
+constexpr int kFP = 2;               // outputs per lane
 constexpr int kFO = kFW * 32 * kFP;  // outputs per CTA
+constexpr int kFK = 8;               // k values whose operands are loaded ahead of their FMAs
 int tiles_flat(int n) { return ceil_div(n * n, kFO); }
 
 template <int NACC, class LA, class LB, class EPI>
@@ -83,15 +85,33 @@ __device__ __forceinline__ void gemm_flat_f64(int n, int t, const LA& la, const 
   for (int a = 0; a < NACC; ++a)
 #pragma unroll
     for (int u = 0; u < kFP; ++u) acc[a][u] = 0.0;
-#pragma unroll 4
-  for (int k = 0; k < n; ++k) {
+  // operands of kFK consecutive k are loaded first, so that every warp keeps
+  // kFK * kFP * (1 + NACC) loads in flight while the FP64 pipe works
+  int k0 = 0;
+  for (; k0 + kFK <= n; k0 += kFK) {
+    double xa[kFK][kFP], xb[kFK][NACC][kFP];
+#pragma unroll
+    for (int kk = 0; kk < kFK; ++kk)
+#pragma unroll
+      for (int u = 0; u < kFP; ++u) {
+        xa[kk][u] = la(ii[u], k0 + kk);
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) xb[kk][a][u] = lb(a, k0 + kk, jj[u]);
+      }
+#pragma unroll
+    for (int kk = 0; kk < kFK; ++kk)
+#pragma unroll
+      for (int u = 0; u < kFP; ++u)
+#pragma unroll
+        for (int a = 0; a < NACC; ++a) acc[a][u] = fma(xa[kk][u], xb[kk][a][u], acc[a][u]);
+  }
+  for (int k = k0; k < n; ++k)
 #pragma unroll
     for (int u = 0; u < kFP; ++u) {
       const double x = la(ii[u], k);
 #pragma unroll
       for (int a = 0; a < NACC; ++a) acc[a][u] = fma(x, lb(a, k, jj[u]), acc[a][u]);
     }
-  }
 #pragma unroll
   for (int u = 0; u < kFP; ++u)
     if (base + 32 * u < nn) epi(ii[u], jj[u], acc[0][u], acc[NACC - 1][u]);
@@ -292,18 +312,19 @@ __device__ __forceinline__ bool j32_rotates(float app, float aqq, float apq, flo
 }
 
 __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
-  extern __shared__ float fsm[];
+  extern __shared__ __align__(16) float fsm[];
   __shared__ float sh_amax;
   Search& s = S[s0 + blockIdx.x];
   if (!mixed_route_due(s)) return;
   constexpr int NW = kJ32NT / 32;
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int lda = N + 1;
+  const int lda = N + 1;            // odd: the 2 x 2 block accesses spread over the banks
+  const int ldv = (N + 3) & ~3;     // V columns start on 16 bytes: float4 rows
   const int nblk = P * (P + 1) / 2;
-  float* A = fsm;
-  float* V = A + lda * N;
-  float2* rcs = reinterpret_cast<float2*>(V + lda * N);  // N lda even: 8-byte aligned
+  float* V = fsm;                   // dynamic shared memory starts 16-byte aligned
+  float* A = V + ldv * N;
+  float2* rcs = reinterpret_cast<float2*>(A + lda * N);  // N lda even: 8-byte aligned
   float* rt = reinterpret_cast<float*>(rcs + P);
   int* rpq = reinterpret_cast<int*>(rt + P);
   int* blk = rpq + P;  // block b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi: Pi | Qi << 16
@@ -322,8 +343,8 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
     float a = 0.f;
     if (i < n && j < n) a = static_cast<float>(0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0));
     A[i + lda * j] = a;
-    V[i + lda * j] = (i == j && i < n) ? 1.f : 0.f;
   }
+  for (int e = tid; e < ldv * N; e += kJ32NT) V[e] = (e % ldv == e / ldv && e / ldv < n) ? 1.f : 0.f;
   for (int Qi = warp; Qi < P; Qi += NW)
     for (int Pi = lane; Pi <= Qi; Pi += 32) blk[Qi * (Qi + 1) / 2 + Pi] = Pi | (Qi << 16);
   __syncthreads();
@@ -415,18 +436,22 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
         if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
         if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
       }
-      // V <- V J: one warp per rotated pair, lanes over the rows
-      for (int pi = warp; pi < P; pi += NW) {
+      // V <- V J: one warp per rotated pair, four rows per lane (float4); the
+      // pairs go to the warps from the last one down, which carry one 2 x 2
+      // block fewer above (rows past n are zero and stay zero)
+      for (int pi = NW - 1 - warp; pi < P; pi += NW) {
         const int w = rpq[pi];
         if (!(w >> 20)) continue;
         const int p = w & 0x3ff, q = (w >> 10) & 0x3ff;
         const float2 cs = rcs[pi];
-        float* vp = V + lda * p;
-        float* vq = V + lda * q;
-        for (int row = lane; row < n; row += 32) {
-          const float x = vp[row], y = vq[row];
-          vp[row] = cs.x * x - cs.y * y;
-          vq[row] = cs.y * x + cs.x * y;
+        float4* vp = reinterpret_cast<float4*>(V + ldv * p);
+        float4* vq = reinterpret_cast<float4*>(V + ldv * q);
+        for (int r4 = lane; r4 < ldv / 4; r4 += 32) {
+          const float4 x = vp[r4], y = vq[r4];
+          vp[r4] = make_float4(cs.x * x.x - cs.y * y.x, cs.x * x.y - cs.y * y.y, cs.x * x.z - cs.y * y.z,
+                               cs.x * x.w - cs.y * y.w);
+          vq[r4] = make_float4(cs.y * x.x + cs.x * y.x, cs.y * x.y + cs.x * y.y, cs.y * x.z + cs.x * y.z,
+                               cs.y * x.w + cs.x * y.w);
         }
       }
       __syncthreads();
@@ -434,14 +459,14 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   }
   for (int e = tid; e < n * n; e += kJ32NT) {
     const int i = e % n, j = e / n;
-    s.F32b[i + n * j] = V[i + lda * j];
+    s.F32b[i + n * j] = V[i + ldv * j];
   }
   if (tid == 0) s.eig_sweeps32 += sweep;
 }
 
 int jacobi32_smem_bytes(int n) {
-  const int N = n + (n & 1), P = N / 2;
-  return 2 * (N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
+  const int N = n + (n & 1), P = N / 2, ldv = (N + 3) & ~3;
+  return (ldv + N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
 }
 
 int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st) {
