@@ -7,7 +7,8 @@
 // searches at once through prefix-summed tile lists; searches that are done or
 // whose eigendecomposition is not due leave their tiles at once. All control
 // decisions (restarts, lambda doubling, the lazy eigendecomposition cadence)
-// are taken on the device, so the host only enqueues work.
+// are taken on the device, so the host only enqueues work, and a whole-batch
+// generation replays one captured CUDA graph per phase.
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -53,6 +54,12 @@ struct cmaes_s {
   std::vector<PendingEvents> pending;
   double phase_ms[kNumPhases] = {0};
   long long phase_launch[kNumPhases] = {0};
+  // one CUDA graph per phase of a whole-batch generation, captured on first
+  // use and replayed (the launch sequence of a handle is fixed: every control
+  // decision is taken on the device); empty until then or after set_problem
+  cudaGraphExec_t gexec[kNumPhases] = {nullptr};
+  long long g_launch[kNumPhases] = {0};
+  bool graphs_ready = false;
 
   TileMap tiles(int kind, int s0, int s1) const {
     TileMap tm;
@@ -273,8 +280,76 @@ static cmaes_status drain_events(cmaes_t h) {
   return CMAES_OK;
 }
 
+static void enqueue_phase(cmaes_t h, int k, int s0, int s1, cudaStream_t st) {
+  switch (k) {
+    case kPhaseSample: enqueue_sample(h, s0, s1, st); break;
+    case kPhaseObjective: enqueue_objective(h, s0, s1, st); break;
+    case kPhaseUpdate: enqueue_update(h, s0, s1, st); break;
+    case kPhaseCov: enqueue_cov(h, s0, s1, st); break;
+    case kPhaseEig: enqueue_eig(h, s0, s1, st); break;
+    default: enqueue_stop(h, s0, s1, st); break;
+  }
+}
+
+static void drop_graphs(cmaes_t h) {
+  for (int k = 0; k < kNumPhases; ++k) {
+    if (h->gexec[k]) cudaGraphExecDestroy(h->gexec[k]);
+    h->gexec[k] = nullptr;
+    h->g_launch[k] = 0;
+  }
+  h->graphs_ready = false;
+}
+
+// Captures each phase of a whole-batch generation into a graph on the handle's
+// stream (nothing runs during capture; the launch counters are restored).
+static cmaes_status ensure_graphs(cmaes_t h) {
+  if (h->graphs_ready) return CMAES_OK;
+  for (int k = 0; k < kNumPhases; ++k) {
+    const long long l0 = h->launches, p0 = h->phase_launch[k];
+    cudaGraph_t g = nullptr;
+    CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
+    enqueue_phase(h, k, 0, h->count, h->stream);
+    const cudaError_t e = cudaStreamEndCapture(h->stream, &g);
+    const long long nl = h->launches - l0;
+    h->launches = l0;
+    h->phase_launch[k] = p0;
+    if (e != cudaSuccess) {
+      if (g) cudaGraphDestroy(g);
+      drop_graphs(h);
+      return set_error(h, CMAES_ECUDA, "capture of phase %d failed: %s", k, cudaGetErrorString(e));
+    }
+    cudaError_t ei = cudaSuccess;
+    if (nl > 0) ei = cudaGraphInstantiate(&h->gexec[k], g, 0);
+    cudaGraphDestroy(g);
+    if (ei != cudaSuccess) {
+      drop_graphs(h);
+      return set_error(h, CMAES_ECUDA, "graph of phase %d: %s", k, cudaGetErrorString(ei));
+    }
+    h->g_launch[k] = nl;
+  }
+  h->graphs_ready = true;
+  return launch_check(h, "graph capture");
+}
+
 static cmaes_status enqueue_generation(cmaes_t h, int s0, int s1, cudaStream_t st, bool with_objective) {
   const bool prof = h->profiling;
+  const bool graphed = (s0 == 0 && s1 == h->count);
+  if (graphed) {
+    cmaes_status rg = ensure_graphs(h);
+    if (rg != CMAES_OK) return rg;
+  }
+  auto run = [&](int k) -> cmaes_status {
+    if (!graphed) {
+      enqueue_phase(h, k, s0, s1, st);
+      return CMAES_OK;
+    }
+    if (h->gexec[k]) {
+      CUDA_TRY(h, cudaGraphLaunch(h->gexec[k], st));
+      h->launches += h->g_launch[k];
+      h->phase_launch[k] += h->g_launch[k];
+    }
+    return CMAES_OK;
+  };
   int base = 0;
   if (prof) {
     const int need = kNumPhases + 1;
@@ -296,19 +371,12 @@ static cmaes_status enqueue_generation(cmaes_t h, int s0, int s1, cudaStream_t s
     return prof ? record_event(h, base + k, st) : CMAES_OK;
   };
   cmaes_status r;
-  if ((r = mark(0)) != CMAES_OK) return r;
-  if (with_objective) enqueue_sample(h, s0, s1, st);
-  if ((r = mark(1)) != CMAES_OK) return r;
-  if (with_objective) enqueue_objective(h, s0, s1, st);
-  if ((r = mark(2)) != CMAES_OK) return r;
-  enqueue_update(h, s0, s1, st);
-  if ((r = mark(3)) != CMAES_OK) return r;
-  enqueue_cov(h, s0, s1, st);
-  if ((r = mark(4)) != CMAES_OK) return r;
-  enqueue_eig(h, s0, s1, st);
-  if ((r = mark(5)) != CMAES_OK) return r;
-  enqueue_stop(h, s0, s1, st);
-  if ((r = mark(6)) != CMAES_OK) return r;
+  for (int k = 0; k < kNumPhases; ++k) {
+    if ((r = mark(k)) != CMAES_OK) return r;
+    if (with_objective || (k != kPhaseSample && k != kPhaseObjective))
+      if ((r = run(k)) != CMAES_OK) return r;
+  }
+  if ((r = mark(kNumPhases)) != CMAES_OK) return r;
   return launch_check(h, "generation");
 }
 
@@ -351,6 +419,7 @@ const char* cmaes_last_error(cmaes_t h) { return h ? h->msg.c_str() : g_create_e
 void cmaes_destroy(cmaes_t h) {
   if (!h) return;
   if (h->stream) cudaStreamSynchronize(h->stream);
+  drop_graphs(h);
   for (cudaEvent_t e : h->pool) cudaEventDestroy(e);
   if (h->arena) cudaFree(h->arena);
   if (h->dS) cudaFree(h->dS);
@@ -623,6 +692,7 @@ cmaes_status cmaes_set_problem(cmaes_t h, int s, int kind, const double* Q, cons
     if (r != CMAES_OK) return r;
     CUDA_TRY(h, cudaStreamSynchronize(h->stream));
   }
+  drop_graphs(h);  // the objective phase's launches depend on the objective kinds
   h->any_rotated = false;
   h->any_sphere = false;
   for (const Search& y : h->hs) {
