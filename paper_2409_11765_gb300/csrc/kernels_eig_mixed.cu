@@ -26,7 +26,9 @@
 //   4. One Newton-Schulz step X <- X + X (I - X^T X) / 2 removes the
 //      second-order loss of orthogonality that large first-order corrections
 //      leave (error e -> 1.5 e^2).
-//   5. A = X^T C X in FP64, B <- X; the FP64 Jacobi then runs on (A, B) as in
+//   5. A = X^T C X in FP64, B <- X; on mixed-precision handles a few rounds of
+//      targeted rotations (k_pair_rounds) take the pairs the refinement left;
+//      the FP64 Jacobi then runs on (A, B) as in
 //      the FP64 path: it rotates what step 3 left (pairs of close eigenvalues),
 //      normally ends at its first quiet step, and delivers the eigenvalues, the
 //      PD guard and the canonical form. On mixed-precision handles the
@@ -469,6 +471,154 @@ int jacobi32_smem_bytes(int n) {
   return (ldv + N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
 }
 
+// Targeted rotations before the cyclic cleanup. After the refinement only a
+// handful of pairs of nearly equal eigenvalues can still pass the FP64 Jacobi
+// test, and the cyclic order would need up to n - 1 mostly empty steps to
+// reach them. Here one CTA per search works on A (EA) and V (B) in global
+// memory for up to kRoundsMax rounds: find every pair that passes the test the
+// cleanup uses (same threshold, same rounding floor), take a disjoint set of
+// the largest ones, apply their exact rotations (columns of A, then rows, then
+// the 2 x 2 blocks set exactly, then V's columns). A round with nothing
+// pending ends the kernel; more than kRoundsList pending pairs leaves them all
+// to the cyclic sweeps, which remain the correctness backstop either way.
+// Mixed-precision handles only: the FP64 handles' stricter floor leaves tens
+// of noise-level pairs, which the cluster's 8 SMs rotate faster than one CTA.
+constexpr int kRoundsNT = 256;
+constexpr int kRoundsMax = 16;
+constexpr int kRoundsList = 256;
+constexpr int kRoundsPick = kEigMixedMaxN / 2;  // every disjoint pending pair
+constexpr double kRoundsTol = 1e-14;  // the cyclic FP64 Jacobi's relative threshold
+
+__global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
+  __shared__ int cnt, npick;
+  // candidate keys: ~(top 48 bits of |a_pq|) << 16 | p << 8 | q, so that an
+  // ascending sort gives the largest entries first and ties by index: the
+  // order, and so the rotations, do not depend on thread timing
+  __shared__ unsigned long long ckey[kRoundsList];
+  __shared__ int pp[kRoundsPick], pq[kRoundsPick];
+  __shared__ double pc[kRoundsPick], ps[kRoundsPick], pt[kRoundsPick];
+  __shared__ double papp[kRoundsPick], paqq[kRoundsPick], papq[kRoundsPick];
+  __shared__ double shr[kRoundsNT / 32];
+  Search& s = S[s0 + blockIdx.x];
+  if (!mixed_route_due(s) || !s.mixed) return;
+  const int n = s.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const long long L = s.ldn;
+  double* A = s.EA;
+  double* V = s.B;
+  double am = 0.0;
+  for (int i = tid; i < n; i += kRoundsNT) am = fmax(am, fabs(A[i + L * i]));
+  const double amax = block_max<kRoundsNT>(am, shr);
+  const double floor_abs = 4.0 * n * 0x1p-53 * amax;  // the cleanup's floor on mixed handles
+  const long long floor_bits = __double_as_longlong(floor_abs);
+  long long rot_total = 0;
+  for (int round = 0; round < kRoundsMax; ++round) {
+    if (tid == 0) cnt = 0;
+    __syncthreads();
+    // every pair p < q; entries at or below the floor are rejected on their
+    // bit pattern (non-negative doubles order as integers)
+    for (int q = warp; q < n; q += kRoundsNT / 32) {
+      const double aqq = A[q + L * q];
+      for (int p = lane; p < q; p += 32) {
+        const double apq = A[p + L * q];
+        if ((__double_as_longlong(apq) & 0x7fffffffffffffffll) <= floor_bits) continue;
+        if (!jacobi_rotates(A[p + L * p], aqq, apq, kRoundsTol * kRoundsTol, floor_abs)) continue;
+        const int k = atomicAdd(&cnt, 1);
+        if (k < kRoundsList) {
+          const unsigned long long mag = static_cast<unsigned long long>(__double_as_longlong(fabs(apq)));
+          ckey[k] = (~(mag >> 16) << 16) | (static_cast<unsigned>(p) << 8) | static_cast<unsigned>(q);
+        }
+      }
+    }
+    __syncthreads();
+    const int c = cnt;
+    if (c == 0 || c > kRoundsList) break;  // done, or too many: the cyclic sweeps take them
+    // bitonic sort of the candidate keys (padded to a power of two)
+    int cap = 1;
+    while (cap < c) cap <<= 1;
+    for (int i = c + tid; i < cap; i += kRoundsNT) ckey[i] = ~0ull;
+    __syncthreads();
+    for (int size = 2; size <= cap; size <<= 1)
+      for (int stride = size >> 1; stride > 0; stride >>= 1) {
+        for (int i = tid; i < cap; i += kRoundsNT) {
+          const int j = i ^ stride;
+          if (j > i) {
+            const bool up = (i & size) == 0;
+            const unsigned long long a = ckey[i], b = ckey[j];
+            if ((a > b) == up) {
+              ckey[i] = b;
+              ckey[j] = a;
+            }
+          }
+        }
+        __syncthreads();
+      }
+    if (tid == 0) {  // greedy disjoint set in key order
+      unsigned used[(kEigMixedMaxN + 31) / 32] = {0};
+      int m = 0;
+      for (int j = 0; j < c && m < kRoundsPick; ++j) {
+        const int p = static_cast<int>((ckey[j] >> 8) & 0xff), q = static_cast<int>(ckey[j] & 0xff);
+        if ((used[p >> 5] >> (p & 31)) & 1u || (used[q >> 5] >> (q & 31)) & 1u) continue;
+        used[p >> 5] |= 1u << (p & 31);
+        used[q >> 5] |= 1u << (q & 31);
+        pp[m] = p;
+        pq[m] = q;
+        ++m;
+      }
+      npick = m;
+    }
+    __syncthreads();
+    const int m = npick;
+    if (tid < m) {
+      const int p = pp[tid], q = pq[tid];
+      const double app = A[p + L * p], aqq = A[q + L * q], apq = A[p + L * q];
+      double t, cc, sn;
+      jacobi_rotation(app, aqq, apq, t, cc, sn);
+      pc[tid] = cc;
+      ps[tid] = sn;
+      pt[tid] = t;
+      papp[tid] = app;
+      paqq[tid] = aqq;
+      papq[tid] = apq;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * n; e += kRoundsNT) {  // A <- A J: columns p, q
+      const int k = e / n, r = e % n;
+      double* ap = A + L * pp[k];
+      double* aq = A + L * pq[k];
+      const double x = ap[r], y = aq[r];
+      ap[r] = pc[k] * x - ps[k] * y;
+      aq[r] = ps[k] * x + pc[k] * y;
+    }
+    __syncthreads();
+    for (int e = tid; e < m * n; e += kRoundsNT) {  // A <- J^T A: rows p, q
+      const int k = e / n, col = e % n;
+      const long long o = L * col;
+      const double x = A[pp[k] + o], y = A[pq[k] + o];
+      A[pp[k] + o] = pc[k] * x - ps[k] * y;
+      A[pq[k] + o] = ps[k] * x + pc[k] * y;
+    }
+    __syncthreads();
+    if (tid < m) {  // exact 2 x 2 diagonal block
+      const int p = pp[tid], q = pq[tid];
+      A[p + L * p] = papp[tid] - pt[tid] * papq[tid];
+      A[q + L * q] = paqq[tid] + pt[tid] * papq[tid];
+      A[p + L * q] = 0.0;
+      A[q + L * p] = 0.0;
+    }
+    for (int e = tid; e < m * n; e += kRoundsNT) {  // V <- V J
+      const int k = e / n, r = e % n;
+      double* vp = V + L * pp[k];
+      double* vq = V + L * pq[k];
+      const double x = vp[r], y = vq[r];
+      vp[r] = pc[k] * x - ps[k] * y;
+      vq[r] = ps[k] * x + pc[k] * y;
+    }
+    rot_total += m;
+    __syncthreads();
+  }
+  if (tid == 0) s.eig_rotations += rot_total;
+}
+
 int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st) {
   if (tflat.total <= 0 || s1 <= s0) return 0;
   int nl = 0;
@@ -495,6 +645,8 @@ int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaSt
   k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_T3);
   k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_A);
   nl += 4;
+  k_pair_rounds<<<s1 - s0, kRoundsNT, 0, st>>>(S, s0);
+  ++nl;
   return nl;
 }
 
