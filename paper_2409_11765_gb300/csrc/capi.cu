@@ -228,7 +228,8 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap sq = h->tiles(TK_SQUARE, s0, s1);
   {
     TileMap tfl = h->tiles(TK_FLAT, s0, s1);
-    const int nl = launch_eig_mixed(h->dS, tfl, s0, s1, h->max_n, st);
+    TileMap tsy = h->tiles(TK_FLATSYM, s0, s1);
+    const int nl = launch_eig_mixed(h->dS, tfl, tsy, s0, s1, h->max_n, st);
     h->launches += nl;
     h->phase_launch[kPhaseEig] += nl;
   }
@@ -513,7 +514,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += 4 * align256(ldn * lc * 8);                 // Z Y X U
     }
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
-    if (eig_refined_route(n)) b += align256(n_ * n_ * 4) + 3 * align256(ldn * n_ * 8);  // F32b EX EG EH
+    if (eig_refined_route(n)) b += 3 * align256(ldn * n_ * 8);  // EX EG EH
     b += align256(lc * 8);                             // f
     b += 2 * align256(lc * 4);                         // order rank
     base[s] = total;
@@ -585,7 +586,6 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.EA = reinterpret_cast<double*>(take(ldn * n_ * 8));
     x.ET = reinterpret_cast<double*>(take(ldn * n_ * 8));
     if (eig_refined_route(x.n)) {
-      x.F32b = reinterpret_cast<float*>(take(n_ * n_ * 4));
       x.EX = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EG = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EH = reinterpret_cast<double*>(take(ldn * n_ * 8));
@@ -633,6 +633,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
         case TK_TCSYM: t = h->mixed ? 16 * tiles_tc_sym(x.n) : 0; break;  // reduce: 16 blocks per tile
         case TK_FLAT: t = eig_refined_route(x.n) ? tiles_flat(x.n) : 0; break;
+        case TK_FLATSYM: t = eig_refined_route(x.n) ? tiles_flat_sym(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

@@ -62,8 +62,7 @@ struct Search {
   float *Y32;         // kp x lam_cap, y = B D z from the FP32 accumulators
   double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation
   double fbest64;     // FP64 value of this generation's best point
-  float *F32b;        // n x n FP32 scratch of the refined eigensolver route (V32)
-  double *EX, *EG, *EH;  // ldn x n FP64 scratch of its refinement steps (with EA, ET)
+  double *EX, *EG, *EH;  // ldn x n FP64 scratch of the refined eigensolver route (with EA, ET)
   int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
@@ -93,7 +92,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -149,7 +148,8 @@ void launch_reeval(Search* S, TileMap tm, cudaStream_t st);
 // mixed-precision eigensolver route (kernels_eig_mixed.cu): FP32 Jacobi
 // sweeps, Newton-Schulz lift to FP64, then the FP64 Jacobi finishes
 int tiles_flat(int n);
-int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st);
+int tiles_flat_sym(int n);
+int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);

@@ -67,31 +67,54 @@ __device__ __forceinline__ bool mixed_route_due(const Search& s) {
 constexpr int kFW = 4;               // warps per CTA
 constexpr int kFP = 2;               // outputs per lane
 constexpr int kFO = kFW * 32 * kFP;  // outputs per CTA
-constexpr int kFK = 8;               // k values whose operands are loaded ahead of their FMAs
+constexpr int kFK = 4;               // k values per batch of the load pipeline
+constexpr int kFOS = kFW * 32;       // outputs per CTA of a symmetric product (one per lane)
 int tiles_flat(int n) { return ceil_div(n * n, kFO); }
+int tiles_flat_sym(int n) { return ceil_div(n * (n + 1) / 2, kFOS); }
 
-template <int NACC, class LA, class LB, class EPI>
+// Column j of the packed upper triangle holds outputs o in [j (j+1)/2, (j+1) (j+2)/2).
+__device__ __forceinline__ void upper_index(int o, int& i, int& j) {
+  int c = static_cast<int>((sqrtf(static_cast<float>(8 * o + 1)) - 1.0f) * 0.5f);
+  while ((c + 1) * (c + 2) / 2 <= o) ++c;
+  while (c * (c + 1) / 2 > o) --c;
+  j = c;
+  i = o - c * (c + 1) / 2;
+}
+
+// SYM: the result is symmetric (X^T C X, X^T X); only i <= j is computed (in
+// packed column order, one output per lane so that the halved work still fills
+// as many CTAs) and the epilogue is called for (i, j) and (j, i).
+template <int NACC, bool SYM = false, class LA, class LB, class EPI>
 __device__ __forceinline__ void gemm_flat_f64(int n, int t, const LA& la, const LB& lb, const EPI& epi) {
+  constexpr int kFP = SYM ? 1 : cmaes_gb300::kFP;
+  constexpr int kFO = kFW * 32 * kFP;
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int base = t * kFO + warp * 32 * kFP + lane;
-  const int nn = n * n;
+  const int nn = SYM ? n * (n + 1) / 2 : n * n;
   int ii[kFP], jj[kFP];
 #pragma unroll
   for (int u = 0; u < kFP; ++u) {
     const int o = base + 32 * u;
-    ii[u] = o < nn ? o % n : 0;  // lanes past the end compute (0, 0) and store nothing
-    jj[u] = o < nn ? o / n : 0;
+    if (o >= nn) {  // lanes past the end compute (0, 0) and store nothing
+      ii[u] = 0;
+      jj[u] = 0;
+    } else if (SYM) {
+      upper_index(o, ii[u], jj[u]);
+    } else {
+      ii[u] = o % n;
+      jj[u] = o / n;
+    }
   }
   double acc[NACC][kFP];
 #pragma unroll
   for (int a = 0; a < NACC; ++a)
 #pragma unroll
     for (int u = 0; u < kFP; ++u) acc[a][u] = 0.0;
-  // operands of kFK consecutive k are loaded first, so that every warp keeps
-  // kFK * kFP * (1 + NACC) loads in flight while the FP64 pipe works
-  int k0 = 0;
-  for (; k0 + kFK <= n; k0 += kFK) {
-    double xa[kFK][kFP], xb[kFK][NACC][kFP];
+  // software pipeline over batches of kFK consecutive k: the operands of the
+  // next batch are loaded before the FMAs of the current one, so L2 latency
+  // overlaps FP64 work
+  double xa0[kFK][kFP], xb0[kFK][NACC][kFP], xa1[kFK][kFP], xb1[kFK][NACC][kFP];
+  auto load = [&](double (&xa)[kFK][kFP], double (&xb)[kFK][NACC][kFP], int k0) {
 #pragma unroll
     for (int kk = 0; kk < kFK; ++kk)
 #pragma unroll
@@ -100,14 +123,26 @@ __device__ __forceinline__ void gemm_flat_f64(int n, int t, const LA& la, const 
 #pragma unroll
         for (int a = 0; a < NACC; ++a) xb[kk][a][u] = lb(a, k0 + kk, jj[u]);
       }
+  };
+  auto fmas = [&](const double (&xa)[kFK][kFP], const double (&xb)[kFK][NACC][kFP]) {
 #pragma unroll
     for (int kk = 0; kk < kFK; ++kk)
 #pragma unroll
       for (int u = 0; u < kFP; ++u)
 #pragma unroll
         for (int a = 0; a < NACC; ++a) acc[a][u] = fma(xa[kk][u], xb[kk][a][u], acc[a][u]);
+  };
+  const int nb = n / kFK;  // full batches; the two register buffers alternate
+  if (nb > 0) load(xa0, xb0, 0);
+  int b = 0;
+  for (; b + 1 < nb; b += 2) {
+    load(xa1, xb1, (b + 1) * kFK);
+    fmas(xa0, xb0);
+    if (b + 2 < nb) load(xa0, xb0, (b + 2) * kFK);
+    fmas(xa1, xb1);
   }
-  for (int k = k0; k < n; ++k)
+  if (b < nb) fmas(xa0, xb0);
+  for (int k = nb * kFK; k < n; ++k)
 #pragma unroll
     for (int u = 0; u < kFP; ++u) {
       const double x = la(ii[u], k);
@@ -116,14 +151,17 @@ __device__ __forceinline__ void gemm_flat_f64(int n, int t, const LA& la, const 
     }
 #pragma unroll
   for (int u = 0; u < kFP; ++u)
-    if (base + 32 * u < nn) epi(ii[u], jj[u], acc[0][u], acc[NACC - 1][u]);
+    if (base + 32 * u < nn) {
+      epi(ii[u], jj[u], acc[0][u], acc[NACC - 1][u]);
+      if (SYM && ii[u] != jj[u]) epi(jj[u], ii[u], acc[0][u], acc[NACC - 1][u]);
+    }
 }
 
 // Buffers of the refinement (ldn x n, FP64): EA, ET, EX, EG, EH plus B.
 enum OaOp {
   OA_W0 = 0,  // (C B)^T                    -> EG   (warm start, C symmetric)
   OA_W1,      // A = (C B)^T B = B^T C B    -> EH
-  OA_X0,      // X0 = B V32                 -> ET, X0^T -> EX
+  OA_X0,      // X0 = B V32 (V32 in EG)     -> ET, X0^T -> EX
   OA_T0,      // T0 = C X0 (ET)             -> EA
   OA_SG0,     // S0 = X0^T T0, G0 = X0^T X0 -> EG, EH   (X0^T in EX)
   OA_E0,      // E0 from (EG, EH)           -> EA
@@ -159,18 +197,18 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int
       const double* TT = s.EG;
       const double* B = s.B;
       double* A = s.EH;
-      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return TT[i + L * k]; },
+      gemm_flat_f64<1, true>(n, t, [=] __device__(int i, int k) { return TT[i + L * k]; },
                        [=] __device__(int, int k, int j) { return B[k + L * j]; },
                        [=] __device__(int i, int j, double v, double) { A[i + L * j] = v; });
       break;
     }
     case OA_X0: {
       const double* B = s.B;
-      const float* V = s.F32b;
+      const double* V = s.EG;
       double* X = s.ET;
       double* XT = s.EX;
       gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return B[i + L * k]; },
-                       [=] __device__(int, int k, int j) { return static_cast<double>(V[k + n * j]); },
+                       [=] __device__(int, int k, int j) { return V[k + L * j]; },
                        [=] __device__(int i, int j, double v, double) {
                          X[i + L * j] = v;
                          XT[j + L * i] = v;
@@ -195,7 +233,7 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int
       double* So = op == OA_SG0 ? s.EG : s.ET;
       double* Go = op == OA_SG0 ? s.EH : s.EX;
       double* lam = s.D;  // scratch until the Jacobi writes D
-      gemm_flat_f64<2>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+      gemm_flat_f64<2, true>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
                        [=] __device__(int a, int k, int j) { return a == 0 ? T[k + L * j] : X[k + L * j]; },
                        [=] __device__(int i, int j, double sv, double gv) {
                          So[i + L * j] = sv;
@@ -223,7 +261,7 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int
       const double* XT = s.ET;
       const double* X = s.B;
       double* M = s.EX;
-      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+      gemm_flat_f64<1, true>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
                        [=] __device__(int, int k, int j) { return X[k + L * j]; },
                        [=] __device__(int i, int j, double v, double) {
                          M[i + L * j] = 0.5 * ((i == j ? 1.0 : 0.0) - v);
@@ -250,7 +288,7 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int
       const double* T = s.EX;
       double* A = s.EA;
       double* B = s.B;
-      gemm_flat_f64<1>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
+      gemm_flat_f64<1, true>(n, t, [=] __device__(int i, int k) { return XT[i + L * k]; },
                        [=] __device__(int, int k, int j) { return T[k + L * j]; },
                        [=] __device__(int i, int j, double v, double) {
                          A[i + L * j] = v;
@@ -302,7 +340,7 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
 }
 
 // FP32 cyclic Jacobi on A32 (from EH, symmetrised and shifted on load) with
-// V32 = I; V32 is written to F32b. Rotations below FP32 resolution are skipped: a pair turns
+// V32 = I; V32 is written to EG in FP64. Rotations below FP32 resolution are skipped: a pair turns
 // only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
 // FP32 arithmetic is cheap here, so a step costs its instruction count: the
 // rotation table is packed (p | q << 10 | rotate << 20, (c, s) as float2),
@@ -459,9 +497,11 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
       __syncthreads();
     }
   }
+  // V32 leaves in FP64 (EG, free between the warm start and the first
+  // refinement step), so the product X0 = B V32 converts nothing in its loop
   for (int e = tid; e < n * n; e += kJ32NT) {
     const int i = e % n, j = e / n;
-    s.F32b[i + n * j] = V[i + ldv * j];
+    s.EG[i + L * j] = static_cast<double>(V[i + ldv * j]);
   }
   if (tid == 0) s.eig_sweeps32 += sweep;
 }
@@ -619,32 +659,37 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
   if (tid == 0) s.eig_rotations += rot_total;
 }
 
-int launch_eig_mixed(Search* S, TileMap tflat, int s0, int s1, int max_n, cudaStream_t st) {
+int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
   if (tflat.total <= 0 || s1 <= s0) return 0;
   int nl = 0;
-  const int gf = tflat.total;
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_W0);
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_W1);
-  nl += 2;
+  const int gf = tflat.total, gs = tsym.total;
+  auto flat = [&](int op) {  // products with a general result
+    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, op);
+    ++nl;
+  };
+  auto sym = [&](int op) {   // products with a symmetric result: upper triangle only
+    k_oa_gemm<<<gs, kFW * 32, 0, st>>>(S, tsym, op);
+    ++nl;
+  };
+  flat(OA_W0);
+  sym(OA_W1);
   const int mn = max_n < kE32Max ? max_n : kE32Max;
   const int bytes = jacobi32_smem_bytes(mn);
   cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   k_jacobi32<<<s1 - s0, kJ32NT, bytes, st>>>(S, s0);
   ++nl;
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_X0);
-  ++nl;
+  flat(OA_X0);
   for (int step = 0; step < 2; ++step) {
-    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_T0 : OA_T1);
-    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_SG0 : OA_SG1);
+    flat(step == 0 ? OA_T0 : OA_T1);
+    sym(step == 0 ? OA_SG0 : OA_SG1);
     k_oa_e<<<gf, kFW * 32, 0, st>>>(S, tflat, step);
-    k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, step == 0 ? OA_U0 : OA_U1);
-    nl += 4;
+    ++nl;
+    flat(step == 0 ? OA_U0 : OA_U1);
   }
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_G2);
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_N2);
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_T3);
-  k_oa_gemm<<<gf, kFW * 32, 0, st>>>(S, tflat, OA_A);
-  nl += 4;
+  sym(OA_G2);
+  flat(OA_N2);
+  flat(OA_T3);
+  sym(OA_A);
   k_pair_rounds<<<s1 - s0, kRoundsNT, 0, st>>>(S, s0);
   ++nl;
   return nl;
