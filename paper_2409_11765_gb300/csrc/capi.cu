@@ -193,8 +193,9 @@ static void enqueue_update(cmaes_t h, int s0, int s1, cudaStream_t st) {
   count_launch(h, kPhaseUpdate, r2.total);
   count_launch(h, kPhaseUpdate, r.total);
   if (h->mixed) {
-    launch_reeval(h->dS, rows, st);
-    count_launch(h, kPhaseUpdate, rows.total);
+    TileMap re = h->tiles(TK_REEVAL, s0, s1);
+    launch_reeval(h->dS, re, st);
+    count_launch(h, kPhaseUpdate, re.total);
   }
   launch_recomb_partial(h->dS, rc, st);
   count_launch(h, kPhaseUpdate, rc.total);
@@ -505,7 +506,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += align256(static_cast<size_t>(tiles_tc_sym(n)) * x.covm_nch * 16384 * 8);
       b += 3 * align256(n_ * kp * esz);                // BDT QTh QTl
       b += align256(kp * lc * esz) + align256(kp * lc * 4);  // Zm Y32
-      b += align256(static_cast<size_t>(ceil_div(n, 256)) * 8);
+      b += align256(static_cast<size_t>(tiles_reeval(n)) * 8);
       b += align256(n_ * 4);                             // lam32
       b += align256(static_cast<size_t>(x.mu_cap) * 4);  // w32
       b += align256(ldn * lc * 8);                     // X
@@ -571,7 +572,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.QTl = take(n_ * kp * esz);
       x.Zm = take(kp * lc * esz);
       x.Y32 = reinterpret_cast<float*>(take(kp * lc * 4));
-      x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(ceil_div(x.n, 256)) * 8));
+      x.fpart = reinterpret_cast<double*>(take(static_cast<size_t>(tiles_reeval(x.n)) * 8));
       x.lam32 = reinterpret_cast<float*>(take(n_ * 4));
       x.w32 = reinterpret_cast<float*>(take(static_cast<size_t>(x.mu_cap) * 4));
     } else {
@@ -633,6 +634,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
         case TK_TCSYM: t = h->mixed ? 16 * tiles_tc_sym(x.n) : 0; break;  // reduce: 16 blocks per tile
         case TK_FLAT: t = eig_refined_route(x.n) ? tiles_flat(x.n) : 0; break;
+        case TK_REEVAL: t = h->mixed ? tiles_reeval(x.n) : 0; break;
         case TK_FLATSYM: t = eig_refined_route(x.n) ? tiles_flat_sym(x.n) : 0; break;
       }
       o[s] = static_cast<int>(acc);

@@ -92,7 +92,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -148,6 +148,8 @@ void launch_reeval(Search* S, TileMap tm, cudaStream_t st);
 // mixed-precision eigensolver route (kernels_eig_mixed.cu): FP32 Jacobi
 // sweeps, Newton-Schulz lift to FP64, then the FP64 Jacobi finishes
 int tiles_flat(int n);
+// 32-row blocks of the FP64 re-evaluation of the best point (one partial sum each)
+__host__ __device__ inline int tiles_reeval(int n) { return (n + 31) / 32; }
 int tiles_flat_sym(int n);
 int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st);
 

@@ -497,7 +497,7 @@ __global__ void __launch_bounds__(256) k_finalize(Search* S, int s0) {
   if (s.mixed && s.obj != 0) {
     // the value that decides the best point and the history is the FP64 one
     double acc = 0.0;
-    for (int t = 0; t < ceil_div(n, 256); ++t) acc += s.fpart[t];
+    for (int t = 0; t < tiles_reeval(n); ++t) acc += s.fpart[t];
     f0 = (s.obj == 2) ? 10.0 * n + acc : acc;
   }
   const bool better = f0 < s.best_f;

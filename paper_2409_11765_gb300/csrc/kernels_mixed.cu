@@ -410,30 +410,42 @@ void launch_tc_cov_reduce(Search* S, TileMap tm, cudaStream_t st) {
 }
 
 // ---------------------- FP64 value of the best point ------------------------
-// Rows [256 t, 256 t + 256) of u = Q (x - x*) for x = X[:, order[0]]; the
-// objective terms of those rows, summed in a fixed order, go to fpart[t].
+// Rows [32 t, 32 t + 32) of u = Q (x - x*) for x = X[:, order[0]]: lane = row
+// (coalesced along Q's columns), the eight warps take eight segments of k, and
+// warp 0 adds the segments in order, forms the objective terms of its rows and
+// sums them in a fixed order into fpart[t].
 __global__ void __launch_bounds__(256) k_reeval(Search* S, TileMap tm) {
-  __shared__ double sh[32];
+  __shared__ double part[8][33];
   int t;
   const int si = find_search(tm, t);
   const Search& s = S[si];
   if (s.done || !s.mixed || s.obj == 0) return;
   const int n = s.n, ldn = s.ldn;
-  const int i = t * 256 + threadIdx.x;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int i = t * 32 + lane;
   const double* x = s.X + static_cast<long long>(ldn) * s.order[0];
+  const int kseg = ceil_div(n, 8), k0 = warp * kseg, k1 = min(n, k0 + kseg);
+  double u = 0.0;
+  if (i < n && s.obj != 3)
+    for (int k = k0; k < k1; ++k) u = fma(s.Q[i + static_cast<long long>(ldn) * k], x[k] - s.xstar[k], u);
+  part[warp][lane] = u;
+  __syncthreads();
+  if (warp != 0) return;
   double g = 0.0;
   if (i < n) {
     if (s.obj == 3) {
       const double r = x[i] - s.xstar[i];
       g = r * r;
     } else {
-      double u = 0.0;
-      for (int k = 0; k < n; ++k) u = fma(s.Q[i + static_cast<long long>(ldn) * k], x[k] - s.xstar[k], u);
-      g = (s.obj == 1) ? s.lamdiag[i] * u * u : u * u - 10.0 * cos((2.0 * 3.141592653589793) * u);
+      double uu = 0.0;
+#pragma unroll
+      for (int w = 0; w < 8; ++w) uu += part[w][lane];
+      g = (s.obj == 1) ? s.lamdiag[i] * uu * uu : uu * uu - 10.0 * cos((2.0 * 3.141592653589793) * uu);
     }
   }
-  const double tot = block_sum<256>(g, sh);
-  if (threadIdx.x == 0) s.fpart[t] = tot;
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) g += __shfl_xor_sync(0xffffffffu, g, o);
+  if (lane == 0) s.fpart[t] = g;
 }
 
 void launch_reeval(Search* S, TileMap tm, cudaStream_t st) {
