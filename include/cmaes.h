@@ -93,6 +93,10 @@ typedef struct cmaes_options {
     double tol_hist_fun;  /* default 1e-12                                     */
     double tol_x_factor;  /* TolX = tol_x_factor * sigma0, default 1e-12       */
     double cond_max;      /* default 1e14                                      */
+    int restart_hold;     /* 0: a stopped descent restarts on the device       */
+                          /* (Algorithm 2). 1: it pauses (cmaes_query reports   */
+                          /* done = 2) until cmaes_restart resumes it, so the   */
+                          /* host can schedule descents (K-Replicated, §3.2.2)  */
 } cmaes_options;
 
 /* Snapshot of one search (checkpoint / resume, and teacher-forced checks).
@@ -175,7 +179,9 @@ cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream);
 cmaes_status cmaes_sync(cmaes_t h);
 
 /* Forces Algorithm 2's restart of search s now (lambda doubled if
- * ipop_double). Errors: ESTATE (search done or ask pending). */
+ * ipop_double); also resumes a search paused by restart_hold (done = 2).
+ * Errors: ESTATE (search done for good, ask pending, or a doubled lambda
+ * beyond the panels allocated at creation). */
 cmaes_status cmaes_restart(cmaes_t h, int s);
 
 /* Best sampled point over all descents of search s (x: n doubles, may be
@@ -195,7 +201,9 @@ cmaes_status cmaes_get_generation(cmaes_t h, int s, double* X, double* f,
                                   int* order);
 
 /* Current lambda, generation, descent number and stop flags of search s (any
- * pointer may be NULL). *done is 1 once the search has ended. Synchronises. */
+ * pointer may be NULL). *done is 1 once the search has ended, 2 while a
+ * descent that stopped waits for cmaes_restart (restart_hold), else 0.
+ * Synchronises. */
 cmaes_status cmaes_query(cmaes_t h, int s, int* lambda, int* gen, int* restart,
                          int* flags, int* done);
 

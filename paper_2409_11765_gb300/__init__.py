@@ -46,7 +46,8 @@ class cmaes_options(ctypes.Structure):
                 ("max_iter", ctypes.c_int), ("stop_mask", ctypes.c_int),
                 ("f_target", ctypes.c_double), ("box_lo", ctypes.c_double),
                 ("box_hi", ctypes.c_double), ("tol_hist_fun", ctypes.c_double),
-                ("tol_x_factor", ctypes.c_double), ("cond_max", ctypes.c_double)]
+                ("tol_x_factor", ctypes.c_double), ("cond_max", ctypes.c_double),
+                ("restart_hold", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)

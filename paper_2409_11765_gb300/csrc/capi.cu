@@ -459,6 +459,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   d.max_iter = opt.max_iter;
   d.stop_mask = opt.stop_mask;
   d.precision = opt.precision;
+  d.restart_hold = opt.restart_hold ? 1 : 0;
   d.f_target = opt.f_target;
   d.box_lo = opt.box_lo;
   d.box_hi = opt.box_hi;
@@ -794,7 +795,7 @@ cmaes_status cmaes_restart(cmaes_t h, int s) {
   Search cur;
   cmaes_status r = read_search(h, s, &cur);
   if (r != CMAES_OK) return r;
-  if (cur.done) return set_error(h, CMAES_ESTATE, "search %d is done", s);
+  if (cur.done == 1) return set_error(h, CMAES_ESTATE, "search %d is done", s);
   if (h->dopt.ipop_double && static_cast<long long>(cur.lam) * 2 > h->hs[s].lam_cap)
     return set_error(h, CMAES_ESTATE, "search %d: restart budget exhausted", s);
   launch_force_restart(h->dS, s, h->dopt, h->stream);

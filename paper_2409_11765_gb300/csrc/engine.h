@@ -26,6 +26,7 @@ struct DevOptions {
   int max_iter;
   int stop_mask;
   int precision;
+  int restart_hold;  // 1: a stopped descent pauses (done = 2) until the host restarts it
   double f_target;
   double box_lo, box_hi;
   double tol_hist_fun, tol_x_factor, cond_max;

@@ -710,6 +710,10 @@ __global__ void __launch_bounds__(256) k_stop(Search* S, int s0, DevOptions o) {
     if (threadIdx.x == 0) s.done = 1;
     return;
   }
+  if (o.restart_hold) {  // the host decides when (and whether) this search restarts
+    if (threadIdx.x == 0) s.done = 2;
+    return;
+  }
   restart_descent<256>(s, o, sh);
 }
 
@@ -719,6 +723,7 @@ void launch_stop(Search* S, int s0, int s1, DevOptions o, cudaStream_t st) {
 
 __global__ void __launch_bounds__(256) k_force_restart(Search* S, int si, DevOptions o) {
   __shared__ double sh[32];
+  if (threadIdx.x == 0) S[si].done = 0;  // resumes a paused search (restart_hold)
   restart_descent<256>(S[si], o, sh);
 }
 
