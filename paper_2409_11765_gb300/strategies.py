@@ -203,7 +203,8 @@ def compare(objective, n, lam_start, kmax, seeds, precision=1, max_gens=4000, ch
     for kind, rs in runs.items():
         out[kind] = {"ert_ms": ert_table(rs, TARGETS, "device_ms"),
                      "ert_evals": ert_table(rs, TARGETS, "evals"),
-                     "candidates_per_s": float(np.mean([r["candidates_per_s"] for r in rs]))}
+                     "candidates_per_s": float(np.mean([r["candidates_per_s"] for r in rs])),
+                     "runs": [{"seed": r["seed"], "best": r["best"], **r["total"]} for r in rs]}
     out["speedup_distributed_over_replicated"] = [
         (a["ert"] / b["ert"]) if math.isfinite(a["ert"]) and math.isfinite(b["ert"]) else None
         for a, b in zip(out["kreplicated"]["ert_ms"], out["kdistributed"]["ert_ms"])]
