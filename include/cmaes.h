@@ -178,6 +178,32 @@ cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream);
 /* Waits for all work of the handle. */
 cmaes_status cmaes_sync(cmaes_t h);
 
+/* Asynchronous, batched ask / tell for an external objective over searches
+ * [s0, s1), for a costly f evaluated on the host while the device works on
+ * other searches (the paper's black-box setting, §1, §4.1). Both calls only
+ * enqueue work on `stream` (NULL: the handle's stream) and return; the caller
+ * synchronises the stream before reading or reusing the host buffers. Host
+ * buffers should be pinned (cudaHostAlloc) for the copies to overlap; pageable
+ * memory works but copies synchronously.
+ *
+ * cmaes_ask_async samples the searches (searches that are done keep their last
+ * points) and copies, per search i = s - s0:
+ *   X[i]            host, n x lambda_cap doubles, column-major, ld n: the
+ *                   panel allocated at creation (lambda_cap = lambda0 *
+ *                   2^max_restarts with ipop_double, else lambda0); the
+ *                   current points are its first lambda columns;
+ *   lam_done[2i]    the current lambda, lam_done[2i + 1] the done flag.
+ * cmaes_tell_async copies f[i] (host, lambda_cap doubles, the first lambda
+ * used) and enqueues the rest of the generation (rank, update, covariance,
+ * eigendecomposition, stop and restart) for the range.
+ * Searches of one range must stay on one stream until its tell; other calls
+ * on those searches wait for the caller's synchronisation.
+ * Errors: EINVAL (range, NULL), ESTATE (ask pending / tell without ask). */
+cmaes_status cmaes_ask_async(cmaes_t h, int s0, int s1, double* const* X,
+                             int* lam_done, void* stream);
+cmaes_status cmaes_tell_async(cmaes_t h, int s0, int s1, const double* const* f,
+                              void* stream);
+
 /* Forces Algorithm 2's restart of search s now (lambda doubled if
  * ipop_double); also resumes a search paused by restart_hold (done = 2).
  * Errors: ESTATE (search done for good, ask pending, or a doubled lambda

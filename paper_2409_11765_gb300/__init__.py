@@ -21,6 +21,7 @@ __all__ = [
     "cmaes_tell", "cmaes_step_batch", "cmaes_sync", "cmaes_restart", "cmaes_best",
     "cmaes_get_state", "cmaes_set_state", "cmaes_get_generation", "cmaes_query",
     "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
+    "cmaes_ask_async", "cmaes_tell_async",
     "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
@@ -104,6 +105,8 @@ def lib():
         "cmaes_kernel_launches": (ctypes.c_longlong, [H]),
         "cmaes_eig_stats": (I, [H, I] + [ctypes.POINTER(ctypes.c_longlong)] * 4),
         "cmaes_evaluate_noalloc": (I, [I, I, I, V, I, V, I, V, V, V, V]),
+        "cmaes_ask_async": (I, [H, I, I, ctypes.POINTER(V), ctypes.POINTER(ctypes.c_int), V]),
+        "cmaes_tell_async": (I, [H, I, I, ctypes.POINTER(V), V]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
         "cmaes_destroy": (None, [H]),
@@ -217,6 +220,19 @@ def cmaes_sync(h):
 
 def cmaes_restart(h, s):
     _check(h, lib().cmaes_restart(h, s))
+
+
+def cmaes_ask_async(h, s0, s1, X_ptrs, lam_done_ptr, stream=None):
+    """X_ptrs: host addresses (ints) of n x lambda_cap FP64 buffers, one per
+    search of [s0, s1); lam_done_ptr: host address of 2 (s1 - s0) ints."""
+    arr = (ctypes.c_void_p * max(1, s1 - s0))(*X_ptrs)  # the C side checks the range
+    _check(h, lib().cmaes_ask_async(h, s0, s1, arr, ctypes.cast(lam_done_ptr, ctypes.POINTER(ctypes.c_int)),
+                                    ctypes.c_void_p(stream) if stream else None))
+
+
+def cmaes_tell_async(h, s0, s1, f_ptrs, stream=None):
+    arr = (ctypes.c_void_p * max(1, s1 - s0))(*f_ptrs)  # the C side checks the range
+    _check(h, lib().cmaes_tell_async(h, s0, s1, arr, ctypes.c_void_p(stream) if stream else None))
 
 
 def cmaes_best(h, s, n):

@@ -10,6 +10,7 @@
 // are taken on the device, so the host only enqueues work, and a whole-batch
 // generation replays one captured CUDA graph per phase.
 #include <cmath>
+#include <cstddef>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -785,6 +786,55 @@ cmaes_status cmaes_tell(cmaes_t h, int s, const double* f_host) {
   if ((r = enqueue_generation(h, s, s + 1, h->stream, false)) != CMAES_OK) return r;
   h->ask_pending[s] = 0;
   CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  return CMAES_OK;
+}
+
+static cmaes_status check_range(cmaes_t h, int s0, int s1) {
+  if (s0 < 0 || s1 > h->count || s0 >= s1)
+    return set_error(h, CMAES_EINVAL, "search range [%d, %d) outside [0, %d)", s0, s1, h->count);
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_ask_async(cmaes_t h, int s0, int s1, double* const* X, int* lam_done, void* stream) {
+  CHECK_HANDLE(h);
+  cmaes_status r = check_range(h, s0, s1);
+  if (r != CMAES_OK) return r;
+  if (!X || !lam_done) return set_error(h, CMAES_EINVAL, "X or lam_done is NULL");
+  for (int s = s0; s < s1; ++s) {
+    if (!X[s - s0]) return set_error(h, CMAES_EINVAL, "X[%d] is NULL", s - s0);
+    if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: ask pending, call tell first", s);
+  }
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  enqueue_sample(h, s0, s1, st);
+  for (int s = s0; s < s1; ++s) {
+    const Search& x = h->hs[s];
+    CUDA_TRY(h, cudaMemcpy2DAsync(X[s - s0], static_cast<size_t>(x.n) * 8, x.X, static_cast<size_t>(x.ldn) * 8,
+                                  static_cast<size_t>(x.n) * 8, x.lam_cap, cudaMemcpyDeviceToHost, st));
+    const char* dev = reinterpret_cast<const char*>(h->dS + s);
+    CUDA_TRY(h, cudaMemcpyAsync(lam_done + 2 * (s - s0), dev + offsetof(Search, lam), sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
+    CUDA_TRY(h, cudaMemcpyAsync(lam_done + 2 * (s - s0) + 1, dev + offsetof(Search, done), sizeof(int),
+                                cudaMemcpyDeviceToHost, st));
+    h->ask_pending[s] = 1;
+  }
+  return launch_check(h, "ask_async");
+}
+
+cmaes_status cmaes_tell_async(cmaes_t h, int s0, int s1, const double* const* f, void* stream) {
+  CHECK_HANDLE(h);
+  cmaes_status r = check_range(h, s0, s1);
+  if (r != CMAES_OK) return r;
+  if (!f) return set_error(h, CMAES_EINVAL, "f is NULL");
+  for (int s = s0; s < s1; ++s) {
+    if (!f[s - s0]) return set_error(h, CMAES_EINVAL, "f[%d] is NULL", s - s0);
+    if (!h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: tell without ask", s);
+  }
+  cudaStream_t st = stream ? static_cast<cudaStream_t>(stream) : h->stream;
+  for (int s = s0; s < s1; ++s)
+    CUDA_TRY(h, cudaMemcpyAsync(h->hs[s].f, f[s - s0], static_cast<size_t>(h->hs[s].lam_cap) * 8,
+                                cudaMemcpyHostToDevice, st));
+  if ((r = enqueue_generation(h, s0, s1, st, false)) != CMAES_OK) return r;
+  for (int s = s0; s < s1; ++s) h->ask_pending[s] = 0;
   return CMAES_OK;
 }
 
