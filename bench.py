@@ -202,6 +202,25 @@ def eig_flops(n, decompositions):
     return (4.0 + 9.0 * 2 + 2.0) * n ** 3 * decompositions
 
 
+# DRAM bytes of the eigendecomposition phase per generation (ncu dram__bytes_read.sum +
+# dram__bytes_write.sum over its kernels, one warm generation of the headline workload; see
+# profiles/eig_traffic_rastrigin-n100-kdist_tf32.md). Valid only for the engine sources it was
+# measured on: any change to them makes the roofline's traffic null until it is measured again.
+EIG_TRAFFIC = {"bytes": 35937792, "sources_sha256_16": "1faf58cbfd277e16"}
+
+
+def engine_sources_sha():
+    import glob
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2409_11765_gb300", "csrc")
+    files = sorted(glob.glob(os.path.join(csrc, "*.cu"))) + sorted(glob.glob(os.path.join(csrc, "*.cuh"))) \
+        + sorted(glob.glob(os.path.join(csrc, "*.h")))
+    h = hashlib.sha256()
+    for f in files:
+        h.update(open(f, "rb").read())
+    return h.hexdigest()[:16]
+
+
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
 
@@ -350,8 +369,11 @@ def run_engine(args):
         peak = bf16 * (0.5 if head == "tf32" else 1.0)
         bound, src = "tensor", ("MEASURED_PEAKS.json bf16 x nominal tf32/bf16 ratio 0.5"
                                 if head == "tf32" else "MEASURED_PEAKS.json bf16")
+    traffic = None
+    if dom == "eig" and head != "fp64" and engine_sources_sha() == EIG_TRAFFIC["sources_sha256_16"]:
+        traffic = EIG_TRAFFIC["bytes"]
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": None, "kernel": dom, "peak_source": src,
+                "frac": achieved / peak, "traffic": traffic, "kernel": dom, "peak_source": src,
                 "algorithmic_flops_per_step": r["phase_flops_per_step"][dom]}
     if rank != 0:
         if dist is not None:
