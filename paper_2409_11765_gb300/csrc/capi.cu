@@ -517,7 +517,11 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += 4 * align256(ldn * lc * 8);                 // Z Y X U
     }
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
-    if (eig_refined_route(n)) b += 3 * align256(ldn * n_ * 8);  // EX EG EH
+    if (eig_refined_route(n)) {
+      b += 3 * align256(ldn * n_ * 8);  // EX EG EH
+      b += align256(static_cast<size_t>(jlog_steps_cap(n)) * jlog_pairs(n) * 8);  // jlog
+      b += align256(static_cast<size_t>(jlog_steps_cap(n)) * 4);                  // jlog_r
+    }
     b += align256(lc * 8);                             // f
     b += 2 * align256(lc * 4);                         // order rank
     base[s] = total;
@@ -592,6 +596,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.EX = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EG = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EH = reinterpret_cast<double*>(take(ldn * n_ * 8));
+      x.jlog = reinterpret_cast<float*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * jlog_pairs(x.n) * 8));
+      x.jlog_r = reinterpret_cast<int*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * 4));
     }
     if (h->mixed) {
       x.X = reinterpret_cast<double*>(take(ldn * lc * 8));

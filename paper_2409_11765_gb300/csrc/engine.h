@@ -64,6 +64,9 @@ struct Search {
   double *fpart;      // ceil(n / 256) partial sums of the FP64 re-evaluation
   double fbest64;     // FP64 value of this generation's best point
   double *EX, *EG, *EH;  // ldn x n FP64 scratch of the refined eigensolver route (with EA, ET)
+  float *jlog;        // FP32 Jacobi rotation log: jlog_steps_cap(n) x jlog_pairs(n) (c, s) pairs
+  int *jlog_r;        // jlog_steps_cap(n): round-robin step index r of each logged step
+  int jlog_steps, jlog_pad_;  // logged steps of the last FP32 Jacobi
   int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
@@ -125,6 +128,12 @@ constexpr int kJacobiClusterN = 256;
 constexpr int kEigMixedMaxN = 160;
 __host__ __device__ inline bool eig_refined_route(int n) { return n > kJacobiSmallN && n <= kEigMixedMaxN; }
 __host__ __device__ inline bool eig_refined_route(const Search& s) { return eig_refined_route(s.n); }
+// The FP32 Jacobi of that route runs at most kJ32MaxSweeps sweeps of N - 1
+// round-robin steps (N = n rounded up to even) and logs the rotations of each
+// step that rotates anything: N / 2 (c, s) pairs, identity for idle pairs.
+constexpr int kJ32MaxSweeps = 20;
+__host__ __device__ inline int jlog_pairs(int n) { return (n + (n & 1)) / 2; }
+__host__ __device__ inline int jlog_steps_cap(int n) { return kJ32MaxSweeps * (n + (n & 1) - 1); }
 void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int lo_n, int hi_n, int max_n,
                            cudaStream_t st);
 void launch_jacobi_cluster(Search* S, int s0, int s1, int lo_n, int hi_n, int layout_n, cudaStream_t st);

@@ -10,9 +10,11 @@
 //   1. A = B^T C B in FP64 (the warm start, from the previous basis B), and
 //      A32 = A - c I in FP32 with c = trace(A) / n.
 //   2. FP32 cyclic Jacobi on A32 (round-robin ordering, the rotation of
-//      Golub & Van Loan §8.5) down to FP32 resolution; V32 collects the
-//      rotations. X0 = B V32 in FP64 is an orthonormal basis to ~1e-7 whose
-//      columns are eigenvectors of C to FP32 accuracy.
+//      Golub & Van Loan §8.5) down to FP32 resolution in one CTA per search;
+//      it logs its rotations, and V32 = their product is formed from the log
+//      by one warp per row across the GPU. X0 = B V32 in FP64 is an
+//      orthonormal basis to ~1e-7 whose columns are eigenvectors of C to FP32
+//      accuracy.
 //   3. Two steps of the iterative refinement of Ogita & Aishima ("Iterative
 //      refinement for symmetric eigenvalue decomposition", Japan J. Indust.
 //      Appl. Math. 35, 2018): with S = X^T C X, G = X^T X, lambda_i = s_ii / g_ii,
@@ -31,10 +33,10 @@
 //      the FP64 Jacobi then runs on (A, B) as in
 //      the FP64 path: it rotates what step 3 left (pairs of close eigenvalues),
 //      normally ends at its first quiet step, and delivers the eigenvalues, the
-//      PD guard and the canonical form. On mixed-precision handles the
-//      off-diagonal entries below n eps64 max|a_ii|, the rounding level of the
-//      product that formed A, are left alone; FP64 handles keep the plain
-//      relative test, so their result matches a full FP64 Jacobi.
+//      PD guard and the canonical form. Off-diagonal entries below
+//      n eps64 max|a_ii| (FP64 handles) or 4 n eps64 max|a_ii| (mixed
+//      handles), the rounding level of the product that formed A, are left
+//      alone.
 // Because X^T X is measured and corrected every decomposition, rounding does
 // not accumulate in B from one generation's warm start to the next.
 // Every FP64 product reads its left operand along its leading dimension
@@ -45,10 +47,9 @@
 
 namespace cmaes_gb300 {
 
-constexpr int kE32Max = kEigMixedMaxN;  // FP32 Jacobi keeps A32 and V32 in shared memory
+constexpr int kE32Max = kEigMixedMaxN;  // FP32 Jacobi keeps A32 in shared memory
 constexpr int kJ32NT = 1024;
 constexpr float kJ32Tol = 1e-6f;
-constexpr int kJ32MaxSweeps = 20;
 
 __device__ __forceinline__ bool mixed_route_due(const Search& s) {
   return !s.done && s.eig_due && eig_refined_route(s);
@@ -339,14 +340,16 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
   }
 }
 
-// FP32 cyclic Jacobi on A32 (from EH, symmetrised and shifted on load) with
-// V32 = I; V32 is written to EG in FP64. Rotations below FP32 resolution are skipped: a pair turns
-// only when |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
+// FP32 cyclic Jacobi on A32 (from EH, symmetrised and shifted on load).
+// Rotations below FP32 resolution are skipped: a pair turns only when
+// |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
 // FP32 arithmetic is cheap here, so a step costs its instruction count: the
 // rotation table is packed (p | q << 10 | rotate << 20, (c, s) as float2),
-// the upper-triangle 2 x 2 blocks come from a table built once, V <- V J runs
-// one warp per pair over the rows, and the rotation count of a step is the
-// barrier's own count.
+// only the upper triangle of A is kept (a_ij at min(i, j) + lda max(i, j)),
+// its 2 x 2 blocks come from a table built once, and the rotation count of a
+// step is the barrier's own count. The eigenvectors are not formed here: each
+// step that rotates anything appends its (c, s) table to the rotation log,
+// and k_jlog_apply replays the log on the rows of V32 = I across the GPU.
 __device__ __forceinline__ bool j32_rotates(float app, float aqq, float apq, float floor_abs) {
   return fabsf(apq) > floor_abs && fabsf(apq) > kJ32Tol * sqrtf(fabsf(app * aqq));
 }
@@ -360,14 +363,13 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int lda = N + 1;            // odd: the 2 x 2 block accesses spread over the banks
-  const int ldv = (N + 3) & ~3;     // V columns start on 16 bytes: float4 rows
   const int nblk = P * (P + 1) / 2;
-  float* V = fsm;                   // dynamic shared memory starts 16-byte aligned
-  float* A = V + ldv * N;
+  float* A = fsm;
   float2* rcs = reinterpret_cast<float2*>(A + lda * N);  // N lda even: 8-byte aligned
   float* rt = reinterpret_cast<float*>(rcs + P);
   int* rpq = reinterpret_cast<int*>(rt + P);
   int* blk = rpq + P;  // block b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi: Pi | Qi << 16
+  auto up = [=](int i, int j) -> float& { return i < j ? A[i + lda * j] : A[j + lda * i]; };
   // A32 = (B^T C B - c I) rounded to FP32, with c the mean eigenvalue (the
   // trace over n, in FP64). The shift leaves the eigenvectors alone and lets
   // FP32 resolve the spread of the spectrum around c, which is where nearly
@@ -384,7 +386,6 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
     if (i < n && j < n) a = static_cast<float>(0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0));
     A[i + lda * j] = a;
   }
-  for (int e = tid; e < ldv * N; e += kJ32NT) V[e] = (e % ldv == e / ldv && e / ldv < n) ? 1.f : 0.f;
   for (int Qi = warp; Qi < P; Qi += NW)
     for (int Pi = lane; Pi <= Qi; Pi += 32) blk[Qi * (Qi + 1) / 2 + Pi] = Pi | (Qi << 16);
   __syncthreads();
@@ -399,17 +400,19 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
   const int M = N - 1;
-  int quiet = 0, sweep = 0;
+  float2* jlog = reinterpret_cast<float2*>(s.jlog);
+  int quiet = 0, sweep = 0, logged = 0;
   bool converged = false;
   for (; sweep < kJ32MaxSweeps && !converged; ++sweep) {
     for (int r = 0; r < M; ++r) {
       int act = 0;
+      float c = 1.f, sn = 0.f;
       if (tid < P) {  // round-robin pair tid of step r (player N - 1 fixed)
         const int p = (tid == 0) ? r : (r + tid) % M;
         const int q = (tid == 0) ? M : (r - tid + M) % M;
-        float c = 1.f, sn = 0.f, tn = 0.f;
+        float tn = 0.f;
         if (p < n && q < n) {
-          const float app = A[p + lda * p], aqq = A[q + lda * q], apq = A[p + lda * q];
+          const float app = A[p + lda * p], aqq = A[q + lda * q], apq = up(p, q);
           if (j32_rotates(app, aqq, apq, floor_abs)) {
             const float theta = (aqq - app) / (2.f * apq);
             const float at = fabsf(theta);
@@ -444,7 +447,11 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
         continue;
       }
       quiet = 0;
-      // A <- J^T A J per 2 x 2 block (pair Pi rows, pair Qi columns, Pi <= Qi), mirrored
+      // at most kJ32MaxSweeps * M steps rotate: the log's capacity
+      if (tid < P) jlog[static_cast<size_t>(logged) * P + tid] = make_float2(c, sn);
+      if (tid == 0) s.jlog_r[logged] = r;
+      ++logged;
+      // A <- J^T A J per 2 x 2 block (pair Pi rows, pair Qi columns, Pi <= Qi)
       for (int b = tid; b < nblk; b += kJ32NT) {
         const int pq = blk[b];
         const int Pi = pq & 0xffff, Qi = pq >> 16;
@@ -452,63 +459,131 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
         if (!((wP | wQ) >> 20)) continue;
         const int p1 = wP & 0x3ff, q1 = (wP >> 10) & 0x3ff, p2 = wQ & 0x3ff, q2 = (wQ >> 10) & 0x3ff;
         if (Pi == Qi) {
-          const float app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
-          const float tt = rt[Pi];
-          A[p1 + lda * p1] = app - tt * apq;
-          A[q1 + lda * q1] = aqq + tt * apq;
-          A[p1 + lda * q1] = 0.f;
-          A[q1 + lda * p1] = 0.f;
+          float& apq = up(p1, q1);
+          const float tt = rt[Pi], a = apq;
+          A[p1 + lda * p1] -= tt * a;
+          A[q1 + lda * q1] += tt * a;
+          apq = 0.f;
           continue;
         }
         const float2 csP = rcs[Pi], csQ = rcs[Qi];
         const float cP = csP.x, sP = csP.y, cQ = csQ.x, sQ = csQ.y;
         const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
-        const float a = (vp1 && vp2) ? A[p1 + lda * p2] : 0.f;
-        const float bb = (vp1 && vq2) ? A[p1 + lda * q2] : 0.f;
-        const float c = (vq1 && vp2) ? A[q1 + lda * p2] : 0.f;
-        const float d = (vq1 && vq2) ? A[q1 + lda * q2] : 0.f;
+        const float a = (vp1 && vp2) ? up(p1, p2) : 0.f;
+        const float bb = (vp1 && vq2) ? up(p1, q2) : 0.f;
+        const float c4 = (vq1 && vp2) ? up(q1, p2) : 0.f;
+        const float d = (vq1 && vq2) ? up(q1, q2) : 0.f;
         const float y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
-        const float y10 = c * cQ - d * sQ, y11 = c * sQ + d * cQ;
-        const float x00 = cP * y00 - sP * y10, x01 = cP * y01 - sP * y11;
-        const float x10 = sP * y00 + cP * y10, x11 = sP * y01 + cP * y11;
-        if (vp1 && vp2) { A[p1 + lda * p2] = x00; A[p2 + lda * p1] = x00; }
-        if (vp1 && vq2) { A[p1 + lda * q2] = x01; A[q2 + lda * p1] = x01; }
-        if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
-        if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
-      }
-      // V <- V J: one warp per rotated pair, four rows per lane (float4); the
-      // pairs go to the warps from the last one down, which carry one 2 x 2
-      // block fewer above (rows past n are zero and stay zero)
-      for (int pi = NW - 1 - warp; pi < P; pi += NW) {
-        const int w = rpq[pi];
-        if (!(w >> 20)) continue;
-        const int p = w & 0x3ff, q = (w >> 10) & 0x3ff;
-        const float2 cs = rcs[pi];
-        float4* vp = reinterpret_cast<float4*>(V + ldv * p);
-        float4* vq = reinterpret_cast<float4*>(V + ldv * q);
-        for (int r4 = lane; r4 < ldv / 4; r4 += 32) {
-          const float4 x = vp[r4], y = vq[r4];
-          vp[r4] = make_float4(cs.x * x.x - cs.y * y.x, cs.x * x.y - cs.y * y.y, cs.x * x.z - cs.y * y.z,
-                               cs.x * x.w - cs.y * y.w);
-          vq[r4] = make_float4(cs.y * x.x + cs.x * y.x, cs.y * x.y + cs.x * y.y, cs.y * x.z + cs.x * y.z,
-                               cs.y * x.w + cs.x * y.w);
-        }
+        const float y10 = c4 * cQ - d * sQ, y11 = c4 * sQ + d * cQ;
+        if (vp1 && vp2) up(p1, p2) = cP * y00 - sP * y10;
+        if (vp1 && vq2) up(p1, q2) = cP * y01 - sP * y11;
+        if (vq1 && vp2) up(q1, p2) = sP * y00 + cP * y10;
+        if (vq1 && vq2) up(q1, q2) = sP * y01 + cP * y11;
       }
       __syncthreads();
     }
   }
-  // V32 leaves in FP64 (EG, free between the warm start and the first
-  // refinement step), so the product X0 = B V32 converts nothing in its loop
-  for (int e = tid; e < n * n; e += kJ32NT) {
-    const int i = e % n, j = e / n;
-    s.EG[i + L * j] = static_cast<double>(V[i + ldv * j]);
+  if (tid == 0) {
+    s.jlog_steps = logged;
+    s.eig_sweeps32 += sweep;
   }
-  if (tid == 0) s.eig_sweeps32 += sweep;
 }
 
 int jacobi32_smem_bytes(int n) {
-  const int N = n + (n & 1), P = N / 2, ldv = (N + 3) & ~3;
-  return (ldv + N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
+  const int N = n + (n & 1), P = N / 2;
+  return (N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
+}
+
+// V32 from the rotation log: row i of V32 = e_i^T J_1 J_2 ... J_T, and the
+// rows are independent, so one warp per row replays the logged steps on its
+// row in shared memory (lane k applies the pairs k, k + 32, k + 64 of a step;
+// the pairs of one step are disjoint, so a step needs only a warp barrier).
+// The log streams through shared memory in chunks of kLogChunk steps (a chunk
+// is contiguous in the log): the CTA's loads of chunk c + 1 are in flight
+// while its warps apply chunk c, so a step waits on shared memory only. The
+// CTA's kLogRows rows leave as FP64 into EG (V32 is read from there by
+// X0 = B V32), 8 consecutive rows of a column per store group.
+constexpr int kLogRows = 8;
+constexpr int kLogNT = kLogRows * 32;
+constexpr int kLogPL = (kE32Max / 2 + 31) / 32;  // pairs per lane
+constexpr int kLogChunk = 32;
+constexpr int kLogChunkMax = kLogChunk * (kE32Max / 2);  // (c, s) entries per chunk
+constexpr int kLogLoads = (kLogChunkMax + kLogNT - 1) / kLogNT;
+
+__global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
+  __shared__ float vrow[kLogRows][kE32Max + 1];
+  __shared__ float2 lcs[2][kLogChunkMax];
+  __shared__ int lr[2][kLogChunk];
+  const Search& s = S[s0 + blockIdx.y];
+  if (!mixed_route_due(s)) return;
+  const int n = s.n, N = n + (n & 1), P = N / 2, M = N - 1;
+  const int i0 = blockIdx.x * kLogRows;
+  if (i0 >= n) return;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, i = i0 + warp;
+  float* v = vrow[warp];
+  for (int j = lane; j < N; j += 32) v[j] = (j == i) ? 1.f : 0.f;  // rows past n stay zero
+  const float2* jlog = reinterpret_cast<const float2*>(s.jlog);
+  const int T = s.jlog_steps;
+  const int nch = ceil_div(T, kLogChunk);
+  float2 stage[kLogLoads];
+  int rstage = 0;
+  auto load = [&](int c) {  // chunk c into registers: entries [c K P, min(T, (c + 1) K) P)
+    const int t0 = c * kLogChunk, cnt = min(kLogChunk, T - t0);
+    const float2* src = jlog + static_cast<size_t>(t0) * P;
+#pragma unroll
+    for (int u = 0; u < kLogLoads; ++u) {
+      const int e = tid + u * kLogNT;
+      if (e < cnt * P) stage[u] = __ldg(src + e);
+    }
+    if (tid < cnt) rstage = __ldg(s.jlog_r + t0 + tid);
+  };
+  auto store = [&](int c, int buf) {
+    const int cnt = min(kLogChunk, T - c * kLogChunk);
+#pragma unroll
+    for (int u = 0; u < kLogLoads; ++u) {
+      const int e = tid + u * kLogNT;
+      if (e < cnt * P) lcs[buf][e] = stage[u];
+    }
+    if (tid < cnt) lr[buf][tid] = rstage;
+  };
+  if (nch > 0) {
+    load(0);
+    store(0, 0);
+  }
+  __syncthreads();
+  for (int c = 0; c < nch; ++c) {
+    const int cur = c & 1;
+    if (c + 1 < nch) load(c + 1);  // in flight during the steps of chunk c
+    const int cnt = min(kLogChunk, T - c * kLogChunk);
+    const float2* cs = lcs[cur];
+    for (int k = 0; k < cnt; ++k, cs += P) {
+      const int r = lr[cur][k];
+#pragma unroll
+      for (int u = 0; u < kLogPL; ++u) {
+        const int pi = lane + 32 * u;
+        if (pi < P) {  // the round-robin pair pi of step r, as in k_jacobi32
+          const float2 g = cs[pi];
+          int p = r + pi, q = r - pi;
+          if (p >= M) p -= M;
+          if (q < 0) q += M;
+          if (pi == 0) q = M;
+          const float x = v[p], y = v[q];
+          v[p] = g.x * x - g.y * y;
+          v[q] = g.y * x + g.x * y;
+        }
+      }
+      __syncwarp();
+    }
+    // the other buffer was last read in chunk c - 1, before the barrier below it
+    if (c + 1 < nch) store(c + 1, cur ^ 1);
+    __syncthreads();
+  }
+  const long long L = s.ldn;
+  const int rows = min(kLogRows, n - i0);
+  for (int e = tid; e < kLogRows * n; e += kLogNT) {
+    const int ii = e % kLogRows, j = e / kLogRows;
+    if (ii < rows) s.EG[(i0 + ii) + L * j] = static_cast<double>(vrow[ii][j]);
+  }
 }
 
 // Targeted rotations before the cyclic cleanup. After the refinement only a
@@ -677,7 +752,8 @@ int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int
   const int bytes = jacobi32_smem_bytes(mn);
   cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
   k_jacobi32<<<s1 - s0, kJ32NT, bytes, st>>>(S, s0);
-  ++nl;
+  k_jlog_apply<<<dim3(ceil_div(mn, kLogRows), s1 - s0), kLogRows * 32, 0, st>>>(S, s0);
+  nl += 2;
   flat(OA_X0);
   for (int step = 0; step < 2; ++step) {
     flat(step == 0 ? OA_T0 : OA_T1);
