@@ -340,19 +340,57 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
   }
 }
 
-// FP32 cyclic Jacobi on A32 (from EH, symmetrised and shifted on load).
-// Rotations below FP32 resolution are skipped: a pair turns only when
-// |a_pq| > 1e-6 sqrt|a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
-// FP32 arithmetic is cheap here, so a step costs its instruction count: the
-// rotation table is packed (p | q << 10 | rotate << 20, (c, s) as float2),
-// only the upper triangle of A is kept (a_ij at min(i, j) + lda max(i, j)),
-// its 2 x 2 blocks come from a table built once, and the rotation count of a
-// step is the barrier's own count. The eigenvectors are not formed here: each
-// step that rotates anything appends its (c, s) table to the rotation log,
-// and k_jlog_apply replays the log on the rows of V32 = I across the GPU.
+// FP32 cyclic Jacobi on A32 (from EH, symmetrised, shifted and scaled on
+// load). Rotations below FP32 resolution are skipped: a pair turns only when
+// a_pq^2 > 1e-12 |a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
+// FP32 arithmetic is cheap here, so a step costs its instruction count and
+// the length of its dependent chains:
+//  - A32 is scaled by a power of two so that max|a_ij| lies in [0.5, 1): the
+//    scaling is exact, leaves the eigenvectors alone, and keeps the squares
+//    of the rotation test and of the angle away from underflow and overflow;
+//  - the rotation (Golub & Van Loan §8.5, t the smaller root of
+//    t^2 + 2 theta t - 1 = 0 with theta = (a_qq - a_pp) / (2 a_pq)) is
+//    taken as t = sign(theta) 2 |a_pq| / (|d| + sqrt(d^2 + 4 a_pq^2)),
+//    d = a_qq - a_pp: one square root and one division, both the fast
+//    approximations; c = 1 / sqrt(1 + t^2) is rsqrtf plus one Newton step,
+//    s = t c. Any t gives an orthogonal (c, s); its last-bit error only
+//    leaves a_pq at FP32 rounding level, which the FP64 refinement removes;
+//  - only the upper triangle of A is kept (a_ij at min(i, j) + lda max(i, j));
+//  - the thread that computes a pair's rotation also updates its 2 x 2
+//    diagonal block (no other thread reads those three entries in the step);
+//  - each thread owns the same off-diagonal 2 x 2 blocks (pair Pi rows, pair
+//    Qi columns, Pi < Qi) in every step, their indices held in registers;
+//  - a pair's step record is one float4 (c, s, p | rotates << 16, q);
+//  - with n odd the padding row and column N - 1 are zero, their pairs never
+//    rotate (c = 1, s = 0), and the block updates keep them exactly zero, so
+//    no update tests an index against n;
+//  - the rotation count of a step is the barrier's own count.
+// The eigenvectors are not formed here: each step that rotates anything
+// appends its (c, s) table to the rotation log, and k_jlog_apply replays the
+// log on the rows of V32 = I across the GPU.
+constexpr float kJ32Tol2 = kJ32Tol * kJ32Tol;
 __device__ __forceinline__ bool j32_rotates(float app, float aqq, float apq, float floor_abs) {
-  return fabsf(apq) > floor_abs && fabsf(apq) > kJ32Tol * sqrtf(fabsf(app * aqq));
+  return fabsf(apq) > floor_abs && apq * apq > kJ32Tol2 * fabsf(app * aqq);
 }
+
+// (c, s, t) of the rotation that annihilates a_pq (a_pq passed j32_rotates,
+// so a_pq^2 > 0 and the root's argument is positive)
+__device__ __forceinline__ void j32_rotation(float app, float aqq, float apq, float& c, float& s, float& t) {
+  const float d = aqq - app;
+  const float x = fmaf(d, d, 4.f * apq * apq);
+  const float h = x * rsqrtf(x);  // sqrt(d^2 + 4 a_pq^2)
+  const float mag = __fdividef(2.f * fabsf(apq), fabsf(d) + h);
+  // sign(theta), with theta = +-0 counted as positive
+  t = (d == 0.f || ((d > 0.f) == (apq > 0.f))) ? mag : -mag;
+  const float u = fmaf(t, t, 1.f);
+  float y = rsqrtf(u);
+  y = y * fmaf(-0.5f * u * y, y, 1.5f);  // Newton step for 1 / sqrt(u)
+  c = y;
+  s = t * y;
+}
+
+// off-diagonal 2 x 2 blocks per thread at the largest size: P (P - 1) / 2 over kJ32NT threads
+constexpr int kJ32Blocks = ((kE32Max / 2) * (kE32Max / 2 - 1) / 2 + kJ32NT - 1) / kJ32NT;
 
 __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   extern __shared__ __align__(16) float fsm[];
@@ -363,15 +401,13 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
   const int lda = N + 1;            // odd: the 2 x 2 block accesses spread over the banks
-  const int nblk = P * (P + 1) / 2;
-  float* A = fsm;
-  float2* rcs = reinterpret_cast<float2*>(A + lda * N);  // N lda even: 8-byte aligned
-  float* rt = reinterpret_cast<float*>(rcs + P);
-  int* rpq = reinterpret_cast<int*>(rt + P);
-  int* blk = rpq + P;  // block b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi: Pi | Qi << 16
+  const int nblk = P * (P - 1) / 2;
+  float4* rinfo = reinterpret_cast<float4*>(fsm);          // P step records
+  float* A = fsm + 4 * P;
   auto up = [=](int i, int j) -> float& { return i < j ? A[i + lda * j] : A[j + lda * i]; };
-  // A32 = (B^T C B - c I) rounded to FP32, with c the mean eigenvalue (the
-  // trace over n, in FP64). The shift leaves the eigenvectors alone and lets
+  // A32 = 2^-k (B^T C B - c I) rounded to FP32, with c the mean eigenvalue
+  // (the trace over n, in FP64) and 2^-k the power of two that brings
+  // max|a_ij| into [0.5, 1). The shift leaves the eigenvectors alone and lets
   // FP32 resolve the spread of the spectrum around c, which is where nearly
   // equal eigenvalues of an early descent (C close to a multiple of I) live.
   const long long L = s.ldn;
@@ -380,14 +416,17 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   for (int i = tid; i < n; i += kJ32NT) tr += A64[i + L * i];
   __shared__ double shs[kJ32NT / 32];
   const double c = block_sum<kJ32NT>(tr, shs) / n;
+  auto a64 = [=](int i, int j) { return 0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0); };
+  double am = 0.0;
+  for (int e = tid; e < n * n; e += kJ32NT) am = fmax(am, fabs(a64(e % n, e / n)));
+  am = block_max<kJ32NT>(am, shs);
+  int ex = 0;
+  if (am > 0.0) frexp(am, &ex);  // am = m 2^ex, m in [0.5, 1)
+  const double scale = ldexp(1.0, -ex);
   for (int e = tid; e < N * N; e += kJ32NT) {
     const int i = e % N, j = e / N;
-    float a = 0.f;
-    if (i < n && j < n) a = static_cast<float>(0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0));
-    A[i + lda * j] = a;
+    A[i + lda * j] = (i < n && j < n) ? static_cast<float>(a64(i, j) * scale) : 0.f;
   }
-  for (int Qi = warp; Qi < P; Qi += NW)
-    for (int Pi = lane; Pi <= Qi; Pi += 32) blk[Qi * (Qi + 1) / 2 + Pi] = Pi | (Qi << 16);
   __syncthreads();
   if (warp == 0) {
     float m = 0.f;
@@ -397,6 +436,17 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
     if (lane == 0) sh_amax = m;
   }
   __syncthreads();
+  // the thread's blocks b = tid + kJ32NT u, b = Qi (Qi - 1) / 2 + Pi, Pi < Qi,
+  // packed Pi | Qi << 16 (-1: none)
+  int bPQ[kJ32Blocks];
+#pragma unroll
+  for (int u = 0; u < kJ32Blocks; ++u) {
+    const int b = tid + kJ32NT * u;
+    int Qi = static_cast<int>(0.5 + sqrt(0.25 + 2.0 * b));
+    while (Qi * (Qi - 1) / 2 > b) --Qi;
+    while ((Qi + 1) * Qi / 2 <= b) ++Qi;
+    bPQ[u] = b < nblk ? (b - Qi * (Qi - 1) / 2) | (Qi << 16) : -1;
+  }
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
   const int M = N - 1;
@@ -406,25 +456,23 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   for (; sweep < kJ32MaxSweeps && !converged; ++sweep) {
     for (int r = 0; r < M; ++r) {
       int act = 0;
-      float c = 1.f, sn = 0.f;
+      float cr = 1.f, sr = 0.f;
       if (tid < P) {  // round-robin pair tid of step r (player N - 1 fixed)
         const int p = (tid == 0) ? r : (r + tid) % M;
         const int q = (tid == 0) ? M : (r - tid + M) % M;
-        float tn = 0.f;
         if (p < n && q < n) {
-          const float app = A[p + lda * p], aqq = A[q + lda * q], apq = up(p, q);
+          float& apq_ref = up(p, q);
+          const float app = A[p + lda * p], aqq = A[q + lda * q], apq = apq_ref;
           if (j32_rotates(app, aqq, apq, floor_abs)) {
-            const float theta = (aqq - app) / (2.f * apq);
-            const float at = fabsf(theta);
-            tn = (at > 1e18f) ? 0.5f / theta : (theta >= 0.f ? 1.f : -1.f) / (at + sqrtf(theta * theta + 1.f));
-            c = 1.f / sqrtf(tn * tn + 1.f);
-            sn = tn * c;
+            float tn;
+            j32_rotation(app, aqq, apq, cr, sr, tn);
+            A[p + lda * p] = app - tn * apq;  // the 2 x 2 diagonal block
+            A[q + lda * q] = aqq + tn * apq;
+            apq_ref = 0.f;
             act = 1;
           }
         }
-        rcs[tid] = make_float2(c, sn);
-        rt[tid] = tn;
-        rpq[tid] = p | (q << 10) | (act << 20);
+        rinfo[tid] = make_float4(cr, sr, __int_as_float(p | (act << 16)), __int_as_float(q));
       }
       const int nact = __syncthreads_count(act);
       if (nact == 0) {
@@ -448,37 +496,29 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
       }
       quiet = 0;
       // at most kJ32MaxSweeps * M steps rotate: the log's capacity
-      if (tid < P) jlog[static_cast<size_t>(logged) * P + tid] = make_float2(c, sn);
+      if (tid < P) jlog[static_cast<size_t>(logged) * P + tid] = make_float2(cr, sr);
       if (tid == 0) s.jlog_r[logged] = r;
       ++logged;
-      // A <- J^T A J per 2 x 2 block (pair Pi rows, pair Qi columns, Pi <= Qi)
-      for (int b = tid; b < nblk; b += kJ32NT) {
-        const int pq = blk[b];
-        const int Pi = pq & 0xffff, Qi = pq >> 16;
-        const int wP = rpq[Pi], wQ = rpq[Qi];
-        if (!((wP | wQ) >> 20)) continue;
-        const int p1 = wP & 0x3ff, q1 = (wP >> 10) & 0x3ff, p2 = wQ & 0x3ff, q2 = (wQ >> 10) & 0x3ff;
-        if (Pi == Qi) {
-          float& apq = up(p1, q1);
-          const float tt = rt[Pi], a = apq;
-          A[p1 + lda * p1] -= tt * a;
-          A[q1 + lda * q1] += tt * a;
-          apq = 0.f;
-          continue;
-        }
-        const float2 csP = rcs[Pi], csQ = rcs[Qi];
-        const float cP = csP.x, sP = csP.y, cQ = csQ.x, sQ = csQ.y;
-        const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
-        const float a = (vp1 && vp2) ? up(p1, p2) : 0.f;
-        const float bb = (vp1 && vq2) ? up(p1, q2) : 0.f;
-        const float c4 = (vq1 && vp2) ? up(q1, p2) : 0.f;
-        const float d = (vq1 && vq2) ? up(q1, q2) : 0.f;
+      // A <- J^T A J on the thread's off-diagonal blocks
+#pragma unroll
+      for (int u = 0; u < kJ32Blocks; ++u) {
+        if (bPQ[u] < 0) continue;
+        const float4 iP = rinfo[bPQ[u] & 0xffff], iQ = rinfo[bPQ[u] >> 16];
+        const int wP = __float_as_int(iP.z), wQ = __float_as_int(iQ.z);
+        if (!((wP | wQ) >> 16)) continue;
+        const int p1 = wP & 0xffff, q1 = __float_as_int(iP.w), p2 = wQ & 0xffff, q2 = __float_as_int(iQ.w);
+        const float cP = iP.x, sP = iP.y, cQ = iQ.x, sQ = iQ.y;
+        float& e00 = up(p1, p2);
+        float& e01 = up(p1, q2);
+        float& e10 = up(q1, p2);
+        float& e11 = up(q1, q2);
+        const float a = e00, bb = e01, c4 = e10, d = e11;
         const float y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
         const float y10 = c4 * cQ - d * sQ, y11 = c4 * sQ + d * cQ;
-        if (vp1 && vp2) up(p1, p2) = cP * y00 - sP * y10;
-        if (vp1 && vq2) up(p1, q2) = cP * y01 - sP * y11;
-        if (vq1 && vp2) up(q1, p2) = sP * y00 + cP * y10;
-        if (vq1 && vq2) up(q1, q2) = sP * y01 + cP * y11;
+        e00 = cP * y00 - sP * y10;
+        e01 = cP * y01 - sP * y11;
+        e10 = sP * y00 + cP * y10;
+        e11 = sP * y01 + cP * y11;
       }
       __syncthreads();
     }
@@ -491,29 +531,74 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
 
 int jacobi32_smem_bytes(int n) {
   const int N = n + (n & 1), P = N / 2;
-  return (N + 1) * N * 4 + P * (8 + 4 + 4) + (P * (P + 1) / 2) * 4 + 16;
+  return P * 16 + (N + 1) * N * 4;
 }
 
 // V32 from the rotation log: row i of V32 = e_i^T J_1 J_2 ... J_T, and the
 // rows are independent, so one warp per row replays the logged steps on its
 // row in shared memory (lane k applies the pairs k, k + 32, k + 64 of a step;
 // the pairs of one step are disjoint, so a step needs only a warp barrier).
-// The log streams through shared memory in chunks of kLogChunk steps (a chunk
-// is contiguous in the log): the CTA's loads of chunk c + 1 are in flight
-// while its warps apply chunk c, so a step waits on shared memory only. The
-// CTA's kLogRows rows leave as FP64 into EG (V32 is read from there by
-// X0 = B V32), 8 consecutive rows of a column per store group.
+// The log streams through shared memory in chunks of whole steps, up to
+// kLogChunkMax (c, s) entries (a chunk is contiguous in the log): the CTA's
+// loads of chunk c + 1 are in flight while its warps apply chunk c, and the
+// CTA turns each entry's step index r and pair index into the packed row
+// indices p | q << 8 once for all its warps. The CTA's kLogRows rows leave as
+// FP64 into EG (V32 is read from there by X0 = B V32), 8 consecutive rows of
+// a column per store group.
 constexpr int kLogRows = 8;
 constexpr int kLogNT = kLogRows * 32;
-constexpr int kLogPL = (kE32Max / 2 + 31) / 32;  // pairs per lane
-constexpr int kLogChunk = 32;
-constexpr int kLogChunkMax = kLogChunk * (kE32Max / 2);  // (c, s) entries per chunk
-constexpr int kLogLoads = (kLogChunkMax + kLogNT - 1) / kLogNT;
+constexpr int kLogChunkMax = 2048;  // (c, s) entries per chunk
+constexpr int kLogLoads = kLogChunkMax / kLogNT;
+static_assert(kE32Max < 256, "row indices are packed in 8 bits");
+
+template <int PL>  // pairs per lane: P <= 32 PL
+__device__ __forceinline__ void jlog_steps(float* v, const float2* cs, const unsigned short* pq, int cnt, int P,
+                                           int lane) {
+  // the records of step k + 1 are read before the row accesses of step k
+  float2 g[PL];
+  int w[PL];
+#pragma unroll
+  for (int u = 0; u < PL; ++u) {
+    const int pi = lane + 32 * u;
+    g[u] = pi < P ? cs[pi] : make_float2(1.f, 0.f);
+    w[u] = pi < P ? pq[pi] : 0;
+  }
+  for (int k = 0; k < cnt; ++k) {
+    float2 gn[PL];
+    int wn[PL];
+    const bool more = k + 1 < cnt;
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int pi = lane + 32 * u, e = (k + 1) * P + pi;
+      gn[u] = (more && pi < P) ? cs[e] : make_float2(1.f, 0.f);
+      wn[u] = (more && pi < P) ? pq[e] : 0;
+    }
+    float x[PL], y[PL];
+#pragma unroll
+    for (int u = 0; u < PL; ++u)
+      if (lane + 32 * u < P) {
+        x[u] = v[w[u] & 0xff];
+        y[u] = v[w[u] >> 8];
+      }
+#pragma unroll
+    for (int u = 0; u < PL; ++u)
+      if (lane + 32 * u < P) {
+        v[w[u] & 0xff] = g[u].x * x[u] - g[u].y * y[u];
+        v[w[u] >> 8] = g[u].y * x[u] + g[u].x * y[u];
+      }
+    __syncwarp();
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      g[u] = gn[u];
+      w[u] = wn[u];
+    }
+  }
+}
 
 __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
   __shared__ float vrow[kLogRows][kE32Max + 1];
   __shared__ float2 lcs[2][kLogChunkMax];
-  __shared__ int lr[2][kLogChunk];
+  __shared__ unsigned short lpq[2][kLogChunkMax];
   const Search& s = S[s0 + blockIdx.y];
   if (!mixed_route_due(s)) return;
   const int n = s.n, N = n + (n & 1), P = N / 2, M = N - 1;
@@ -524,27 +609,37 @@ __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
   for (int j = lane; j < N; j += 32) v[j] = (j == i) ? 1.f : 0.f;  // rows past n stay zero
   const float2* jlog = reinterpret_cast<const float2*>(s.jlog);
   const int T = s.jlog_steps;
-  const int nch = ceil_div(T, kLogChunk);
+  const int K = kLogChunkMax / P;  // steps per chunk
+  const int nch = ceil_div(T, K);
   float2 stage[kLogLoads];
-  int rstage = 0;
+  int rstage[kLogLoads];
   auto load = [&](int c) {  // chunk c into registers: entries [c K P, min(T, (c + 1) K) P)
-    const int t0 = c * kLogChunk, cnt = min(kLogChunk, T - t0);
+    const int t0 = c * K, cnt = min(K, T - t0);
     const float2* src = jlog + static_cast<size_t>(t0) * P;
 #pragma unroll
     for (int u = 0; u < kLogLoads; ++u) {
       const int e = tid + u * kLogNT;
-      if (e < cnt * P) stage[u] = __ldg(src + e);
+      if (e < cnt * P) {
+        stage[u] = __ldg(src + e);
+        rstage[u] = __ldg(s.jlog_r + t0 + e / P);
+      }
     }
-    if (tid < cnt) rstage = __ldg(s.jlog_r + t0 + tid);
   };
   auto store = [&](int c, int buf) {
-    const int cnt = min(kLogChunk, T - c * kLogChunk);
+    const int cnt = min(K, T - c * K);
 #pragma unroll
     for (int u = 0; u < kLogLoads; ++u) {
       const int e = tid + u * kLogNT;
-      if (e < cnt * P) lcs[buf][e] = stage[u];
+      if (e < cnt * P) {
+        const int pi = e % P, r = rstage[u];  // the round-robin pair pi of step r, as in k_jacobi32
+        int p = r + pi, q = r - pi;
+        if (p >= M) p -= M;
+        if (q < 0) q += M;
+        if (pi == 0) q = M;
+        lcs[buf][e] = stage[u];
+        lpq[buf][e] = static_cast<unsigned short>(p | (q << 8));
+      }
     }
-    if (tid < cnt) lr[buf][tid] = rstage;
   };
   if (nch > 0) {
     load(0);
@@ -554,26 +649,13 @@ __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
   for (int c = 0; c < nch; ++c) {
     const int cur = c & 1;
     if (c + 1 < nch) load(c + 1);  // in flight during the steps of chunk c
-    const int cnt = min(kLogChunk, T - c * kLogChunk);
-    const float2* cs = lcs[cur];
-    for (int k = 0; k < cnt; ++k, cs += P) {
-      const int r = lr[cur][k];
-#pragma unroll
-      for (int u = 0; u < kLogPL; ++u) {
-        const int pi = lane + 32 * u;
-        if (pi < P) {  // the round-robin pair pi of step r, as in k_jacobi32
-          const float2 g = cs[pi];
-          int p = r + pi, q = r - pi;
-          if (p >= M) p -= M;
-          if (q < 0) q += M;
-          if (pi == 0) q = M;
-          const float x = v[p], y = v[q];
-          v[p] = g.x * x - g.y * y;
-          v[q] = g.y * x + g.x * y;
-        }
-      }
-      __syncwarp();
-    }
+    const int cnt = min(K, T - c * K);
+    if (P <= 32)
+      jlog_steps<1>(v, lcs[cur], lpq[cur], cnt, P, lane);
+    else if (P <= 64)
+      jlog_steps<2>(v, lcs[cur], lpq[cur], cnt, P, lane);
+    else
+      jlog_steps<3>(v, lcs[cur], lpq[cur], cnt, P, lane);
     // the other buffer was last read in chunk c - 1, before the barrier below it
     if (c + 1 < nch) store(c + 1, cur ^ 1);
     __syncthreads();

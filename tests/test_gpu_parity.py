@@ -37,6 +37,8 @@ def _states(ns, stream0=0, cond=1e3):
     (100, 1088, 1),   # several rank / recombination chunks
     (33, 20, 1),      # smallest cluster-Jacobi size: two CTAs of the cluster idle
     (130, 40, 1),     # cluster Jacobi
+    (159, 30, 2),     # refined route, odd n: the padding pair of the FP32 Jacobi
+    (160, 40, 1),     # largest refined-route size: four 2 x 2 blocks per FP32 Jacobi thread
     (256, 30, 2),     # largest cluster-Jacobi size
     (300, 40, 1),     # global-memory Jacobi
 ])
