@@ -360,6 +360,11 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
 //    diagonal block (no other thread reads those three entries in the step);
 //  - each thread owns the same off-diagonal 2 x 2 blocks (pair Pi rows, pair
 //    Qi columns, Pi < Qi) in every step, their indices held in registers;
+//  - a step after a rotating one costs one barrier: the owner of the block
+//    that holds a pair's next pivot forms that pair's next rotation right
+//    after its own update (the diagonal entries it needs were written in the
+//    step before), so the rotations of step r + 1 are ready when the updates
+//    of step r are; after a quiet step the rotations come from A directly;
 //  - a pair's step record is one float4 (c, s, p | rotates << 16, q);
 //  - with n odd the padding row and column N - 1 are zero, their pairs never
 //    rotate (c = 1, s = 0), and the block updates keep them exactly zero, so
@@ -389,8 +394,11 @@ __device__ __forceinline__ void j32_rotation(float app, float aqq, float apq, fl
   s = t * y;
 }
 
-// off-diagonal 2 x 2 blocks per thread at the largest size: P (P - 1) / 2 over kJ32NT threads
-constexpr int kJ32Blocks = ((kE32Max / 2) * (kE32Max / 2 - 1) / 2 + kJ32NT - 1) / kJ32NT;
+// off-diagonal 2 x 2 blocks per thread at the largest size: one for every
+// thread, then the rest of P (P - 1) / 2 over the kJ32NT - P threads that
+// form no rotation
+constexpr int kJ32Blocks =
+    1 + ((kE32Max / 2) * (kE32Max / 2 - 1) / 2 - kJ32NT + (kJ32NT - kE32Max / 2) - 1) / (kJ32NT - kE32Max / 2);
 
 __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   extern __shared__ __align__(16) float fsm[];
@@ -402,8 +410,8 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   const int lane = tid & 31, warp = tid >> 5;
   const int lda = N + 1;            // odd: the 2 x 2 block accesses spread over the banks
   const int nblk = P * (P - 1) / 2;
-  float4* rinfo = reinterpret_cast<float4*>(fsm);          // P step records
-  float* A = fsm + 4 * P;
+  float4* rinfo = reinterpret_cast<float4*>(fsm);          // 2 x P step records
+  float* A = fsm + 8 * P;
   auto up = [=](int i, int j) -> float& { return i < j ? A[i + lda * j] : A[j + lda * i]; };
   // A32 = 2^-k (B^T C B - c I) rounded to FP32, with c the mean eigenvalue
   // (the trace over n, in FP64) and 2^-k the power of two that brings
@@ -436,161 +444,321 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
     if (lane == 0) sh_amax = m;
   }
   __syncthreads();
-  // the thread's blocks b = tid + kJ32NT u, b = Qi (Qi - 1) / 2 + Pi, Pi < Qi,
-  // packed Pi | Qi << 16 (-1: none)
-  int bPQ[kJ32Blocks];
+  // Each thread owns the same off-diagonal blocks (Pi, Qi), Pi < Qi, in every
+  // step: entry tid of a list, and entries kJ32NT + (kJ32NT - P)(u - 1) +
+  // tid - P for u >= 1 when tid >= P (the threads that form rotations own one
+  // block). The list starts with the P role
+  // blocks, block k holding after its update the pivot of pair k of the next
+  // step, followed by the other blocks column by column. From step r to
+  // r + 1 the round-robin pair pi takes the p of pair pi + 1 and the q of
+  // pair pi - 1 (pair 0: the p of pair 1 and the fixed N - 1; pair 1: the p
+  // of pair 0; pair P - 1: the q of pairs P - 1 and P - 2), so the role
+  // blocks are (0, 1), (0, 2), (pi - 1, pi + 1) and (P - 2, P - 1), with the
+  // pivot at entry (q1, p2), (p1, p2), (q1, p2) and (q1, q2) for the block's
+  // row pair (p1, q1) and column pair (p2, q2). Putting them first keeps the
+  // rotation arithmetic of a step in the first warps, without divergence.
+  // bPQ: Pi | Qi << 16 (-1: none); brole: np | entry << 8, entry 0, 2, 3 =
+  // (p1, p2), (q1, p2), (q1, q2) (-1: none).
+  int bPQ[kJ32Blocks], brole[kJ32Blocks];
 #pragma unroll
   for (int u = 0; u < kJ32Blocks; ++u) {
-    const int b = tid + kJ32NT * u;
-    int Qi = static_cast<int>(0.5 + sqrt(0.25 + 2.0 * b));
-    while (Qi * (Qi - 1) / 2 > b) --Qi;
-    while ((Qi + 1) * Qi / 2 <= b) ++Qi;
-    bPQ[u] = b < nblk ? (b - Qi * (Qi - 1) / 2) | (Qi << 16) : -1;
+    const int k = u == 0 ? tid : (tid >= P ? kJ32NT + (kJ32NT - P) * (u - 1) + tid - P : nblk);
+    int Pi = 0, Qi = 0, ro = -1;
+    if (k < P) {
+      if (k == 0) { Pi = 0; Qi = 1; ro = 0 | (2 << 8); }
+      else if (k == 1) { Pi = 0; Qi = 2; ro = 1 | (0 << 8); }
+      else if (k == P - 1) { Pi = P - 2; Qi = P - 1; ro = (P - 1) | (3 << 8); }
+      else { Pi = k - 1; Qi = k + 1; ro = k | (2 << 8); }
+    } else if (k < nblk) {
+      // the (k - P)-th block that holds no pivot: column Qi has Qi blocks, of
+      // which (0, 1), (Qi - 2, Qi) and (P - 2, P - 1) hold one
+      int j = k - P;
+      Qi = 1;
+      for (;;) {
+        const int cnt = Qi - (Qi == 1) - (Qi >= 2) - (Qi == P - 1);
+        if (j < cnt) break;
+        j -= cnt;
+        ++Qi;
+      }
+      for (Pi = 0;; ++Pi) {
+        const bool role = (Qi == 1 && Pi == 0) || (Pi == Qi - 2) || (Qi == P - 1 && Pi == P - 2);
+        if (role) continue;
+        if (j == 0) break;
+        --j;
+      }
+    }
+    bPQ[u] = k < nblk ? Pi | (Qi << 16) : -1;
+    brole[u] = ro;
   }
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
   const int M = N - 1;
+  const int cap = jlog_steps_cap(n);
   float2* jlog = reinterpret_cast<float2*>(s.jlog);
-  int quiet = 0, sweep = 0, logged = 0;
+  int logged = 0;
+  // The rotation of pair np of step rn from A (its diagonal entries in A,
+  // its pivot apq given): applies the 2 x 2 diagonal block, stores the step
+  // record and the log entry (at the index the step gets if it rotates
+  // anything: later rotating steps overwrite the entries of a quiet one), and
+  // returns whether it rotates. The caller stores the pivot (zero if so).
+  auto rotate_pair = [&](int rn, int np, int pn, int qn, float apq, float4* rec) -> int {
+    float cr = 1.f, sr = 0.f;
+    int act = 0;
+    if (pn < n && qn < n) {
+      const float app = A[pn + lda * pn], aqq = A[qn + lda * qn];
+      if (j32_rotates(app, aqq, apq, floor_abs)) {
+        float tn;
+        j32_rotation(app, aqq, apq, cr, sr, tn);
+        A[pn + lda * pn] = app - tn * apq;
+        A[qn + lda * qn] = aqq + tn * apq;
+        act = 1;
+      }
+    }
+    rec[np] = make_float4(cr, sr, __int_as_float(pn | (act << 16)), __int_as_float(qn));
+    if (logged < cap) {
+      jlog[static_cast<size_t>(logged) * P + np] = make_float2(cr, sr);
+      if (np == 0) s.jlog_r[logged] = rn;
+    }
+    return act;
+  };
+  // the rotations of step rn formed from A alone (the first step, and the
+  // step after a quiet one): pair tid
+  auto rotation_phase = [&](int rn, float4* rec) -> int {
+    int act = 0;
+    if (tid < P) {
+      const int p = (tid == 0) ? rn : (rn + tid) % M;
+      const int q = (tid == 0) ? M : (rn - tid + M) % M;
+      float& apq = up(p, q);
+      act = rotate_pair(rn, tid, p, q, apq, rec);
+      if (act) apq = 0.f;
+    }
+    return act;
+  };
+  auto rec = [=](int b) { return rinfo + b * P; };
+  int cur = 0, r = 0, sweep = 0, quiet = 0;
   bool converged = false;
-  for (; sweep < kJ32MaxSweeps && !converged; ++sweep) {
-    for (int r = 0; r < M; ++r) {
-      int act = 0;
-      float cr = 1.f, sr = 0.f;
-      if (tid < P) {  // round-robin pair tid of step r (player N - 1 fixed)
-        const int p = (tid == 0) ? r : (r + tid) % M;
-        const int q = (tid == 0) ? M : (r - tid + M) % M;
-        if (p < n && q < n) {
-          float& apq_ref = up(p, q);
-          const float app = A[p + lda * p], aqq = A[q + lda * q], apq = apq_ref;
-          if (j32_rotates(app, aqq, apq, floor_abs)) {
-            float tn;
-            j32_rotation(app, aqq, apq, cr, sr, tn);
-            A[p + lda * p] = app - tn * apq;  // the 2 x 2 diagonal block
-            A[q + lda * q] = aqq + tn * apq;
-            apq_ref = 0.f;
-            act = 1;
-          }
+  int nact = __syncthreads_count(rotation_phase(0, rec(0)));
+  while (true) {
+    // step r: its rotations are in rec(cur) (diagonal blocks applied)
+    if (nact == 0) {
+      // a quiet step: if no off-diagonal entry passes the test any more, the
+      // remaining quiet steps of the window would change nothing
+      ++quiet;
+      if (quiet == 1 || (quiet & 15) == 0) {
+        int pend = 0;
+        for (int Qi = warp; Qi < n && !pend; Qi += NW) {
+          const float aqq = A[Qi + lda * Qi];
+          for (int Pi = lane; Pi < Qi; Pi += 32)
+            pend |= j32_rotates(A[Pi + lda * Pi], aqq, A[Pi + lda * Qi], floor_abs);
         }
-        rinfo[tid] = make_float4(cr, sr, __int_as_float(p | (act << 16)), __int_as_float(q));
+        if (!__syncthreads_or(pend)) quiet = M;
       }
-      const int nact = __syncthreads_count(act);
-      if (nact == 0) {
-        // a quiet step: if no off-diagonal entry passes the test any more, the
-        // remaining quiet steps of the window would change nothing
-        ++quiet;
-        if (quiet == 1 || (quiet & 15) == 0) {
-          int pend = 0;
-          for (int Qi = warp; Qi < n && !pend; Qi += NW) {
-            const float aqq = A[Qi + lda * Qi];
-            for (int Pi = lane; Pi < Qi; Pi += 32)
-              pend |= j32_rotates(A[Pi + lda * Pi], aqq, A[Pi + lda * Qi], floor_abs);
-          }
-          if (!__syncthreads_or(pend)) quiet = M;
-        }
-        if (quiet >= M) {
-          converged = true;
-          break;  // uniform: the counts come from block barriers
-        }
-        continue;
+      if (quiet >= M) {
+        converged = true;
+        break;  // uniform: the counts come from block barriers
       }
+    } else {
       quiet = 0;
-      // at most kJ32MaxSweeps * M steps rotate: the log's capacity
-      if (tid < P) jlog[static_cast<size_t>(logged) * P + tid] = make_float2(cr, sr);
-      if (tid == 0) s.jlog_r[logged] = r;
-      ++logged;
-      // A <- J^T A J on the thread's off-diagonal blocks
+      ++logged;  // its log entries were written with its rotations
+    }
+    const int rn = (r + 1 == M) ? 0 : r + 1;
+    if (rn == 0 && ++sweep == kJ32MaxSweeps) break;
+    int act = 0;
+    if (nact == 0) {
+      act = rotation_phase(rn, rec(cur ^ 1));
+    } else {
+      // A <- J^T A J on the thread's off-diagonal blocks, and the rotations
+      // of step rn whose pivots these blocks hold
+      const float4* ri = rec(cur);
 #pragma unroll
       for (int u = 0; u < kJ32Blocks; ++u) {
         if (bPQ[u] < 0) continue;
-        const float4 iP = rinfo[bPQ[u] & 0xffff], iQ = rinfo[bPQ[u] >> 16];
+        const float4 iP = ri[bPQ[u] & 0xffff], iQ = ri[bPQ[u] >> 16];
         const int wP = __float_as_int(iP.z), wQ = __float_as_int(iQ.z);
-        if (!((wP | wQ) >> 16)) continue;
+        const bool rot = (wP | wQ) >> 16;
+        const int ro = brole[u];
+        if (!rot && ro < 0) continue;
         const int p1 = wP & 0xffff, q1 = __float_as_int(iP.w), p2 = wQ & 0xffff, q2 = __float_as_int(iQ.w);
-        const float cP = iP.x, sP = iP.y, cQ = iQ.x, sQ = iQ.y;
         float& e00 = up(p1, p2);
         float& e01 = up(p1, q2);
         float& e10 = up(q1, p2);
         float& e11 = up(q1, q2);
-        const float a = e00, bb = e01, c4 = e10, d = e11;
-        const float y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
-        const float y10 = c4 * cQ - d * sQ, y11 = c4 * sQ + d * cQ;
-        e00 = cP * y00 - sP * y10;
-        e01 = cP * y01 - sP * y11;
-        e10 = sP * y00 + cP * y10;
-        e11 = sP * y01 + cP * y11;
+        float x00 = e00, x01 = e01, x10 = e10, x11 = e11;
+        if (rot) {
+          const float cP = iP.x, sP = iP.y, cQ = iQ.x, sQ = iQ.y;
+          const float y00 = x00 * cQ - x01 * sQ, y01 = x00 * sQ + x01 * cQ;
+          const float y10 = x10 * cQ - x11 * sQ, y11 = x10 * sQ + x11 * cQ;
+          x00 = cP * y00 - sP * y10;
+          x01 = cP * y01 - sP * y11;
+          x10 = sP * y00 + cP * y10;
+          x11 = sP * y01 + cP * y11;
+        }
+        if (ro >= 0) {
+          const int ent = ro >> 8;
+          const int pn = ent == 3 ? q2 : p2, qn = ent == 0 ? p1 : q1;
+          const float apq = ent == 0 ? x00 : (ent == 2 ? x10 : x11);
+          const int a = rotate_pair(rn, ro & 0xff, pn, qn, apq, rec(cur ^ 1));
+          act |= a;
+          if (a) {
+            if (ent == 0) x00 = 0.f;
+            else if (ent == 2) x10 = 0.f;
+            else x11 = 0.f;
+          }
+        }
+        e00 = x00;
+        e01 = x01;
+        e10 = x10;
+        e11 = x11;
       }
-      __syncthreads();
     }
+    nact = __syncthreads_count(act);
+    cur ^= 1;
+    r = rn;
   }
   if (tid == 0) {
     s.jlog_steps = logged;
-    s.eig_sweeps32 += sweep;
+    s.eig_sweeps32 += converged ? sweep + 1 : sweep;
   }
 }
 
 int jacobi32_smem_bytes(int n) {
   const int N = n + (n & 1), P = N / 2;
-  return P * 16 + (N + 1) * N * 4;
+  return 2 * P * 16 + (N + 1) * N * 4;
 }
 
 // V32 from the rotation log: row i of V32 = e_i^T J_1 J_2 ... J_T, and the
-// rows are independent, so one warp per row replays the logged steps on its
-// row in shared memory (lane k applies the pairs k, k + 32, k + 64 of a step;
-// the pairs of one step are disjoint, so a step needs only a warp barrier).
+// rows are independent, so one warp replays the log on one row, held in
+// registers. At step r lane l of slot u holds, for the round-robin pair
+// pi = l + 32 u, a_pi = v[p(r, pi)] and b_pi = v[q(r, pi)]; the rotation of
+// the pair is then local to the lane. From step r to r + 1 (mod N - 1) the
+// ring a_0, a_1, ..., a_{P-1}, b_{P-1}, ..., b_1 moves one place (b_0 = v[N - 1]
+// stays): a_pi <- a_{pi+1}, b_pi <- b_{pi-1}, a_{P-1} <- b_{P-1}, b_1 <- a_0,
+// two shuffles per slot plus one broadcast. Steps the Jacobi did not log (no
+// rotation) are extra moves of the ring.
 // The log streams through shared memory in chunks of whole steps, up to
 // kLogChunkMax (c, s) entries (a chunk is contiguous in the log): the CTA's
-// loads of chunk c + 1 are in flight while its warps apply chunk c, and the
-// CTA turns each entry's step index r and pair index into the packed row
-// indices p | q << 8 once for all its warps. The CTA's kLogRows rows leave as
-// FP64 into EG (V32 is read from there by X0 = B V32), 8 consecutive rows of
-// a column per store group.
+// loads of chunk c + 1 are in flight while its warps apply chunk c. The CTA's
+// kLogRows rows leave as FP64 into EG (V32 is read from there by X0 = B V32),
+// 8 consecutive rows of a column per store group.
 constexpr int kLogRows = 8;
 constexpr int kLogNT = kLogRows * 32;
 constexpr int kLogChunkMax = 2048;  // (c, s) entries per chunk
 constexpr int kLogLoads = kLogChunkMax / kLogNT;
-static_assert(kE32Max < 256, "row indices are packed in 8 bits");
+constexpr int kLogStepsMax = kLogChunkMax / 16;  // steps per chunk at the smallest P (n > 32)
+static_assert(kJacobiSmallN >= 32, "the refined route starts above n = 32: P >= 17");
 
-template <int PL>  // pairs per lane: P <= 32 PL
-__device__ __forceinline__ void jlog_steps(float* v, const float2* cs, const unsigned short* pq, int cnt, int P,
-                                           int lane) {
-  // the records of step k + 1 are read before the row accesses of step k
-  float2 g[PL];
-  int w[PL];
+// round-robin pair pi of step r (N - 1 = M): (r, M) for pi = 0, else
+// ((r + pi) mod M, (r - pi) mod M), as in k_jacobi32
+__device__ __forceinline__ void rr_pair(int r, int pi, int M, int& p, int& q) {
+  p = r + pi;
+  q = r - pi;
+  if (p >= M) p -= M;
+  if (q < 0) q += M;
+  if (pi == 0) q = M;
+}
+
+template <int PL>  // slots per lane: P <= 32 PL
+__device__ __forceinline__ void jlog_replay(const Search& s, float* v, float2 (*lcs)[kLogChunkMax],
+                                            int (*lr)[kLogStepsMax]) {
+  const int n = s.n, N = n + (n & 1), P = N / 2, M = N - 1;
+  const int tid = threadIdx.x, lane = tid & 31;
+  const float2* jlog = reinterpret_cast<const float2*>(s.jlog);
+  const int T = s.jlog_steps;
+  const int K = kLogChunkMax / P;  // steps per chunk (<= kLogStepsMax)
+  const int nch = ceil_div(T, K);
+  float2 stage[kLogLoads];
+  int rstage = 0;
+  auto load = [&](int c) {  // chunk c into registers: entries [c K P, min(T, (c + 1) K) P)
+    const int t0 = c * K, cnt = min(K, T - t0);
+    const float2* src = jlog + static_cast<size_t>(t0) * P;
+#pragma unroll
+    for (int u = 0; u < kLogLoads; ++u) {
+      const int e = tid + u * kLogNT;
+      if (e < cnt * P) stage[u] = __ldg(src + e);
+    }
+    if (tid < cnt) rstage = __ldg(s.jlog_r + t0 + tid);
+  };
+  auto store = [&](int c, int buf) {
+    const int cnt = min(K, T - c * K);
+#pragma unroll
+    for (int u = 0; u < kLogLoads; ++u) {
+      const int e = tid + u * kLogNT;
+      if (e < cnt * P) lcs[buf][e] = stage[u];
+    }
+    if (tid < cnt) lr[buf][tid] = rstage;
+  };
+  if (nch == 0) return;  // no rotation: the row stays e_i
+  load(0);
+  store(0, 0);
+  __syncthreads();
+  // the ring at the first logged step
+  int r = lr[0][0];
+  float a[PL], b[PL];
 #pragma unroll
   for (int u = 0; u < PL; ++u) {
     const int pi = lane + 32 * u;
-    g[u] = pi < P ? cs[pi] : make_float2(1.f, 0.f);
-    w[u] = pi < P ? pq[pi] : 0;
-  }
-  for (int k = 0; k < cnt; ++k) {
-    float2 gn[PL];
-    int wn[PL];
-    const bool more = k + 1 < cnt;
-#pragma unroll
-    for (int u = 0; u < PL; ++u) {
-      const int pi = lane + 32 * u, e = (k + 1) * P + pi;
-      gn[u] = (more && pi < P) ? cs[e] : make_float2(1.f, 0.f);
-      wn[u] = (more && pi < P) ? pq[e] : 0;
+    a[u] = b[u] = 0.f;
+    if (pi < P) {
+      int p, q;
+      rr_pair(r, pi, M, p, q);
+      a[u] = v[p];
+      b[u] = v[q];
     }
-    float x[PL], y[PL];
-#pragma unroll
-    for (int u = 0; u < PL; ++u)
-      if (lane + 32 * u < P) {
-        x[u] = v[w[u] & 0xff];
-        y[u] = v[w[u] >> 8];
-      }
-#pragma unroll
-    for (int u = 0; u < PL; ++u)
-      if (lane + 32 * u < P) {
-        v[w[u] & 0xff] = g[u].x * x[u] - g[u].y * y[u];
-        v[w[u] >> 8] = g[u].y * x[u] + g[u].x * y[u];
-      }
-    __syncwarp();
+  }
+  auto shift = [&]() {  // step r -> r + 1
+    float ra[PL], rb[PL];
 #pragma unroll
     for (int u = 0; u < PL; ++u) {
-      g[u] = gn[u];
-      w[u] = wn[u];
+      ra[u] = __shfl_sync(0xffffffffu, a[u], (lane + 1) & 31);
+      rb[u] = __shfl_sync(0xffffffffu, b[u], (lane - 1) & 31);
+    }
+    const float a00 = __shfl_sync(0xffffffffu, a[0], 0);
+#pragma unroll
+    for (int u = 0; u < PL; ++u) {
+      const int pi = lane + 32 * u;
+      const float up_next = lane < 31 ? ra[u] : (u + 1 < PL ? ra[u + 1 < PL ? u + 1 : u] : 0.f);
+      const float dn_prev = lane > 0 ? rb[u] : (u > 0 ? rb[u > 0 ? u - 1 : 0] : 0.f);
+      const float na = pi == P - 1 ? b[u] : up_next;
+      const float nb = pi == 0 ? b[u] : (pi == 1 ? a00 : dn_prev);
+      a[u] = na;
+      b[u] = nb;
+    }
+  };
+  for (int c = 0; c < nch; ++c) {
+    const int cur = c & 1;
+    if (c + 1 < nch) load(c + 1);  // in flight during the steps of chunk c
+    const int cnt = min(K, T - c * K);
+    const float2* cs = lcs[cur];
+    for (int k = 0; k < cnt; ++k, cs += P) {
+      const int rk = lr[cur][k];
+      int moves = rk - r;  // unlogged steps between the two logged ones, plus one
+      if (moves < 0) moves += M;
+      for (int j = 0; j < moves; ++j) shift();
+      r = rk;
+#pragma unroll
+      for (int u = 0; u < PL; ++u) {
+        const int pi = lane + 32 * u;
+        if (pi < P) {
+          const float2 g = cs[pi];
+          const float x = a[u], y = b[u];
+          a[u] = g.x * x - g.y * y;
+          b[u] = g.y * x + g.x * y;
+        }
+      }
+    }
+    // the other buffer was last read in chunk c - 1, before the barrier below it
+    if (c + 1 < nch) store(c + 1, cur ^ 1);
+    __syncthreads();
+  }
+  __syncwarp();
+#pragma unroll
+  for (int u = 0; u < PL; ++u) {
+    const int pi = lane + 32 * u;
+    if (pi < P) {
+      int p, q;
+      rr_pair(r, pi, M, p, q);
+      v[p] = a[u];
+      v[q] = b[u];
     }
   }
 }
@@ -598,68 +766,23 @@ __device__ __forceinline__ void jlog_steps(float* v, const float2* cs, const uns
 __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
   __shared__ float vrow[kLogRows][kE32Max + 1];
   __shared__ float2 lcs[2][kLogChunkMax];
-  __shared__ unsigned short lpq[2][kLogChunkMax];
+  __shared__ int lr[2][kLogStepsMax];
   const Search& s = S[s0 + blockIdx.y];
   if (!mixed_route_due(s)) return;
-  const int n = s.n, N = n + (n & 1), P = N / 2, M = N - 1;
+  const int n = s.n, N = n + (n & 1), P = N / 2;
   const int i0 = blockIdx.x * kLogRows;
   if (i0 >= n) return;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, i = i0 + warp;
   float* v = vrow[warp];
   for (int j = lane; j < N; j += 32) v[j] = (j == i) ? 1.f : 0.f;  // rows past n stay zero
-  const float2* jlog = reinterpret_cast<const float2*>(s.jlog);
-  const int T = s.jlog_steps;
-  const int K = kLogChunkMax / P;  // steps per chunk
-  const int nch = ceil_div(T, K);
-  float2 stage[kLogLoads];
-  int rstage[kLogLoads];
-  auto load = [&](int c) {  // chunk c into registers: entries [c K P, min(T, (c + 1) K) P)
-    const int t0 = c * K, cnt = min(K, T - t0);
-    const float2* src = jlog + static_cast<size_t>(t0) * P;
-#pragma unroll
-    for (int u = 0; u < kLogLoads; ++u) {
-      const int e = tid + u * kLogNT;
-      if (e < cnt * P) {
-        stage[u] = __ldg(src + e);
-        rstage[u] = __ldg(s.jlog_r + t0 + e / P);
-      }
-    }
-  };
-  auto store = [&](int c, int buf) {
-    const int cnt = min(K, T - c * K);
-#pragma unroll
-    for (int u = 0; u < kLogLoads; ++u) {
-      const int e = tid + u * kLogNT;
-      if (e < cnt * P) {
-        const int pi = e % P, r = rstage[u];  // the round-robin pair pi of step r, as in k_jacobi32
-        int p = r + pi, q = r - pi;
-        if (p >= M) p -= M;
-        if (q < 0) q += M;
-        if (pi == 0) q = M;
-        lcs[buf][e] = stage[u];
-        lpq[buf][e] = static_cast<unsigned short>(p | (q << 8));
-      }
-    }
-  };
-  if (nch > 0) {
-    load(0);
-    store(0, 0);
-  }
+  __syncwarp();
+  if (P <= 32)
+    jlog_replay<1>(s, v, lcs, lr);
+  else if (P <= 64)
+    jlog_replay<2>(s, v, lcs, lr);
+  else
+    jlog_replay<3>(s, v, lcs, lr);
   __syncthreads();
-  for (int c = 0; c < nch; ++c) {
-    const int cur = c & 1;
-    if (c + 1 < nch) load(c + 1);  // in flight during the steps of chunk c
-    const int cnt = min(K, T - c * K);
-    if (P <= 32)
-      jlog_steps<1>(v, lcs[cur], lpq[cur], cnt, P, lane);
-    else if (P <= 64)
-      jlog_steps<2>(v, lcs[cur], lpq[cur], cnt, P, lane);
-    else
-      jlog_steps<3>(v, lcs[cur], lpq[cur], cnt, P, lane);
-    // the other buffer was last read in chunk c - 1, before the barrier below it
-    if (c + 1 < nch) store(c + 1, cur ^ 1);
-    __syncthreads();
-  }
   const long long L = s.ldn;
   const int rows = min(kLogRows, n - i0);
   for (int e = tid; e < kLogRows * n; e += kLogNT) {
