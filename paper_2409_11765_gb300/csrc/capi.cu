@@ -48,6 +48,7 @@ struct cmaes_s {
   std::vector<int> ask_pending;
   int max_n = 0, max_n_small_jacobi = 0, max_n_cluster_jacobi = 0, max_n_global_jacobi = 0;
   bool any_rotated = false, any_sphere = false;
+  bool any_plain_eig = false;  // a search outside the refined eigensolver route (warm start B^T C B by k_eig_gemm_*)
   long long launches = 0;
   // profiling
   bool profiling = false;
@@ -235,10 +236,12 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
     h->launches += nl;
     h->phase_launch[kPhaseEig] += nl;
   }
-  launch_eig_gemm_CB(h->dS, sq, st);
-  count_launch(h, kPhaseEig, sq.total);
-  launch_eig_gemm_BtT(h->dS, sq, st);
-  count_launch(h, kPhaseEig, sq.total);
+  if (h->any_plain_eig) {
+    launch_eig_gemm_CB(h->dS, sq, st);
+    count_launch(h, kPhaseEig, sq.total);
+    launch_eig_gemm_BtT(h->dS, sq, st);
+    count_launch(h, kPhaseEig, sq.total);
+  }
   if (h->max_n_small_jacobi > 0) {
     launch_jacobi_variant(h->dS, s0, s1, true, 0, kJacobiSmallN, h->max_n_small_jacobi, st);
     count_launch(h, kPhaseEig, s1 - s0);
@@ -251,10 +254,11 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
     launch_jacobi_variant(h->dS, s0, s1, false, kJacobiClusterN, 1 << 30, h->max_n_global_jacobi, st);
     count_launch(h, kPhaseEig, s1 - s0);
   }
-  launch_set_bd(h->dS, sq, st);
-  count_launch(h, kPhaseEig, sq.total);
   if (h->mixed) {
-    launch_tc_set_bdt(h->dS, sq, h->opt.precision, 0, st);
+    launch_tc_set_bd_bdt(h->dS, sq, h->opt.precision, st);  // B diag(D) in FP64 and in the operand format
+    count_launch(h, kPhaseEig, sq.total);
+  } else {
+    launch_set_bd(h->dS, sq, st);
     count_launch(h, kPhaseEig, sq.total);
   }
 }
@@ -527,6 +531,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     base[s] = total;
     total += b;
     if (n > h->max_n) h->max_n = n;
+    if (!eig_refined_route(n)) h->any_plain_eig = true;
     int* jm = n <= kJacobiSmallN ? &h->max_n_small_jacobi
               : n <= kJacobiClusterN ? &h->max_n_cluster_jacobi : &h->max_n_global_jacobi;
     if (n > *jm) *jm = n;

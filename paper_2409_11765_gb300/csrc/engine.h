@@ -150,6 +150,7 @@ void tc_cov_split(int n, int mu_cap, int* kc, int* nch);
 int tc_elem_bytes(int precision);
 void launch_tc_prepare_q(Search* S, int s, int precision, cudaStream_t st);
 void launch_tc_set_bdt(Search* S, TileMap tm, int precision, int force, cudaStream_t st);
+void launch_tc_set_bd_bdt(Search* S, TileMap tm, int precision, cudaStream_t st);  // BD and BDT together
 void launch_tc_sample(Search* S, TileMap tm, int precision, cudaStream_t st);
 void launch_tc_objective(Search* S, TileMap tm, int precision, cudaStream_t st);
 void launch_tc_cov_partial(Search* S, TileMap tm, int precision, cudaStream_t st);

@@ -345,9 +345,10 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
 // a_pq^2 > 1e-12 |a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
 // FP32 arithmetic is cheap here, so a step costs its instruction count and
 // the length of its dependent chains:
-//  - A32 is scaled by a power of two so that max|a_ij| lies in [0.5, 1): the
-//    scaling is exact, leaves the eigenvectors alone, and keeps the squares
-//    of the rotation test and of the angle away from underflow and overflow;
+//  - A32 is scaled by a power of two so that max|a_ij| <= 1: the scaling is
+//    exact, leaves the eigenvectors alone, and keeps the squares of the
+//    rotation test and of the angle away from overflow (and, for any spread
+//    FP32 can resolve, from underflow);
 //  - the rotation (Golub & Van Loan §8.5, t the smaller root of
 //    t^2 + 2 theta t - 1 = 0 with theta = (a_qq - a_pp) / (2 a_pq)) is
 //    taken as t = sign(theta) 2 |a_pq| / (|d| + sqrt(d^2 + 4 a_pq^2)),
@@ -414,26 +415,41 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   float* A = fsm + 8 * P;
   auto up = [=](int i, int j) -> float& { return i < j ? A[i + lda * j] : A[j + lda * i]; };
   // A32 = 2^-k (B^T C B - c I) rounded to FP32, with c the mean eigenvalue
-  // (the trace over n, in FP64) and 2^-k the power of two that brings
-  // max|a_ij| into [0.5, 1). The shift leaves the eigenvectors alone and lets
-  // FP32 resolve the spread of the spectrum around c, which is where nearly
-  // equal eigenvalues of an early descent (C close to a multiple of I) live.
+  // (the trace over n, in FP64) and 2^k the power of two at or above
+  // max a_ii. B^T C B is positive semi-definite, so |a_ij| <= max a_ii and
+  // |a_ii - c| <= max a_ii: every entry of A32 is at most one in magnitude.
+  // The shift leaves the eigenvectors alone and lets FP32 resolve the spread
+  // of the spectrum around c, which is where nearly equal eigenvalues of an
+  // early descent (C close to a multiple of I) live. EH is exactly symmetric
+  // (the product writes both triangles), so it is read once, a warp per
+  // column with the column's loads issued together.
   const long long L = s.ldn;
   const double* A64 = s.EH;
-  double tr = 0.0;
-  for (int i = tid; i < n; i += kJ32NT) tr += A64[i + L * i];
+  double tr = 0.0, dmax = 0.0;
+  for (int i = tid; i < n; i += kJ32NT) {
+    const double d = A64[i + L * i];
+    tr += d;
+    dmax = fmax(dmax, fabs(d));
+  }
   __shared__ double shs[kJ32NT / 32];
   const double c = block_sum<kJ32NT>(tr, shs) / n;
-  auto a64 = [=](int i, int j) { return 0.5 * (A64[i + L * j] + A64[j + L * i]) - (i == j ? c : 0.0); };
-  double am = 0.0;
-  for (int e = tid; e < n * n; e += kJ32NT) am = fmax(am, fabs(a64(e % n, e / n)));
-  am = block_max<kJ32NT>(am, shs);
+  dmax = block_max<kJ32NT>(dmax, shs);
   int ex = 0;
-  if (am > 0.0) frexp(am, &ex);  // am = m 2^ex, m in [0.5, 1)
+  if (dmax > 0.0) frexp(dmax, &ex);  // dmax = m 2^ex, m in [0.5, 1)
   const double scale = ldexp(1.0, -ex);
-  for (int e = tid; e < N * N; e += kJ32NT) {
-    const int i = e % N, j = e / N;
-    A[i + lda * j] = (i < n && j < n) ? static_cast<float>(a64(i, j) * scale) : 0.f;
+  constexpr int kRow = (kE32Max + 31) / 32;
+  for (int j = warp; j < N; j += NW) {
+    double x[kRow];
+#pragma unroll
+    for (int u = 0; u < kRow; ++u) {
+      const int i = lane + 32 * u;
+      x[u] = (i < n && j < n) ? A64[i + L * j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRow; ++u) {
+      const int i = lane + 32 * u;
+      if (i < N) A[i + lda * j] = (i < n && j < n) ? static_cast<float>((x[u] - (i == j ? c : 0.0)) * scale) : 0.f;
+    }
   }
   __syncthreads();
   if (warp == 0) {
@@ -801,15 +817,19 @@ __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
 // the 2 x 2 blocks set exactly, then V's columns). A round with nothing
 // pending ends the kernel; more than kRoundsList pending pairs leaves them all
 // to the cyclic sweeps, which remain the correctness backstop either way.
+// A lives in shared memory for the whole kernel (leading dimension n + 1, up to
+// 161 x 160 doubles) and goes back to EA only if a rotation was applied: a
+// round then costs shared-memory passes instead of a scan of A through L2.
 // Mixed-precision handles only: the FP64 handles' stricter floor leaves tens
 // of noise-level pairs, which the cluster's 8 SMs rotate faster than one CTA.
-constexpr int kRoundsNT = 256;
+constexpr int kRoundsNT = 512;
 constexpr int kRoundsMax = 16;
-constexpr int kRoundsList = 256;
+constexpr int kRoundsList = 512;
 constexpr int kRoundsPick = kEigMixedMaxN / 2;  // every disjoint pending pair
 constexpr double kRoundsTol = 1e-14;  // the cyclic FP64 Jacobi's relative threshold
 
 __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
+  extern __shared__ double As[];  // A, leading dimension n + 1
   __shared__ int cnt, npick;
   // candidate keys: ~(top 48 bits of |a_pq|) << 16 | p << 8 | q, so that an
   // ascending sort gives the largest entries first and ties by index: the
@@ -823,10 +843,28 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
   if (!mixed_route_due(s) || !s.mixed) return;
   const int n = s.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long L = s.ldn;
-  double* A = s.EA;
+  double* Ag = s.EA;
   double* V = s.B;
+  const int la = n + 1;
+  constexpr int kRow = (kEigMixedMaxN + 31) / 32;  // rows per lane of a column
+  // a warp per column, its loads issued together (one L2 round trip per column)
+  for (int j = warp; j < n; j += kRoundsNT / 32) {
+    double x[kRow];
+#pragma unroll
+    for (int u = 0; u < kRow; ++u) {
+      const int i = lane + 32 * u;
+      x[u] = i < n ? Ag[i + L * j] : 0.0;
+    }
+#pragma unroll
+    for (int u = 0; u < kRow; ++u) {
+      const int i = lane + 32 * u;
+      if (i < n) As[i + la * j] = x[u];
+    }
+  }
+  __syncthreads();
+  double* A = As;
   double am = 0.0;
-  for (int i = tid; i < n; i += kRoundsNT) am = fmax(am, fabs(A[i + L * i]));
+  for (int i = tid; i < n; i += kRoundsNT) am = fmax(am, fabs(A[i + la * i]));
   const double amax = block_max<kRoundsNT>(am, shr);
   const double floor_abs = 4.0 * n * 0x1p-53 * amax;  // the cleanup's floor on mixed handles
   const long long floor_bits = __double_as_longlong(floor_abs);
@@ -837,14 +875,22 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     // every pair p < q; entries at or below the floor are rejected on their
     // bit pattern (non-negative doubles order as integers)
     for (int q = warp; q < n; q += kRoundsNT / 32) {
-      const double aqq = A[q + L * q];
-      for (int p = lane; p < q; p += 32) {
-        const double apq = A[p + L * q];
-        if ((__double_as_longlong(apq) & 0x7fffffffffffffffll) <= floor_bits) continue;
-        if (!jacobi_rotates(A[p + L * p], aqq, apq, kRoundsTol * kRoundsTol, floor_abs)) continue;
+      const long long* col = reinterpret_cast<const long long*>(A + la * q);
+      long long bits[kRow];  // |a_pq| as integers, loaded together
+#pragma unroll
+      for (int u = 0; u < kRow; ++u) {
+        const int p = lane + 32 * u;
+        bits[u] = p < q ? (col[p] & 0x7fffffffffffffffll) : 0;
+      }
+#pragma unroll
+      for (int u = 0; u < kRow; ++u) {
+        if (bits[u] <= floor_bits) continue;  // the FP64 test only above the floor
+        const int p = lane + 32 * u;
+        const double apq = A[p + la * q];
+        if (!jacobi_rotates(A[p + la * p], A[q + la * q], apq, kRoundsTol * kRoundsTol, floor_abs)) continue;
         const int k = atomicAdd(&cnt, 1);
         if (k < kRoundsList) {
-          const unsigned long long mag = static_cast<unsigned long long>(__double_as_longlong(fabs(apq)));
+          const unsigned long long mag = static_cast<unsigned long long>(bits[u]);
           ckey[k] = (~(mag >> 16) << 16) | (static_cast<unsigned>(p) << 8) | static_cast<unsigned>(q);
         }
       }
@@ -890,7 +936,7 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     const int m = npick;
     if (tid < m) {
       const int p = pp[tid], q = pq[tid];
-      const double app = A[p + L * p], aqq = A[q + L * q], apq = A[p + L * q];
+      const double app = A[p + la * p], aqq = A[q + la * q], apq = A[p + la * q];
       double t, cc, sn;
       jacobi_rotation(app, aqq, apq, t, cc, sn);
       pc[tid] = cc;
@@ -903,8 +949,8 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     __syncthreads();
     for (int e = tid; e < m * n; e += kRoundsNT) {  // A <- A J: columns p, q
       const int k = e / n, r = e % n;
-      double* ap = A + L * pp[k];
-      double* aq = A + L * pq[k];
+      double* ap = A + la * pp[k];
+      double* aq = A + la * pq[k];
       const double x = ap[r], y = aq[r];
       ap[r] = pc[k] * x - ps[k] * y;
       aq[r] = ps[k] * x + pc[k] * y;
@@ -912,7 +958,7 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     __syncthreads();
     for (int e = tid; e < m * n; e += kRoundsNT) {  // A <- J^T A: rows p, q
       const int k = e / n, col = e % n;
-      const long long o = L * col;
+      const int o = la * col;
       const double x = A[pp[k] + o], y = A[pq[k] + o];
       A[pp[k] + o] = pc[k] * x - ps[k] * y;
       A[pq[k] + o] = ps[k] * x + pc[k] * y;
@@ -920,10 +966,10 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     __syncthreads();
     if (tid < m) {  // exact 2 x 2 diagonal block
       const int p = pp[tid], q = pq[tid];
-      A[p + L * p] = papp[tid] - pt[tid] * papq[tid];
-      A[q + L * q] = paqq[tid] + pt[tid] * papq[tid];
-      A[p + L * q] = 0.0;
-      A[q + L * p] = 0.0;
+      A[p + la * p] = papp[tid] - pt[tid] * papq[tid];
+      A[q + la * q] = paqq[tid] + pt[tid] * papq[tid];
+      A[p + la * q] = 0.0;
+      A[q + la * p] = 0.0;
     }
     for (int e = tid; e < m * n; e += kRoundsNT) {  // V <- V J
       const int k = e / n, r = e % n;
@@ -936,8 +982,14 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
     rot_total += m;
     __syncthreads();
   }
+  if (rot_total > 0)  // uniform: every thread counts the same rounds
+    for (int j = warp; j < n; j += kRoundsNT / 32)
+      for (int i = lane; i < n; i += 32) Ag[i + L * j] = As[i + la * j];
   if (tid == 0) s.eig_rotations += rot_total;
 }
+
+int pair_rounds_smem_bytes(int n) { return (n + 1) * n * 8; }
+
 
 int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
   if (tflat.total <= 0 || s1 <= s0) return 0;
@@ -971,7 +1023,9 @@ int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int
   flat(OA_N2);
   flat(OA_T3);
   sym(OA_A);
-  k_pair_rounds<<<s1 - s0, kRoundsNT, 0, st>>>(S, s0);
+  const int rbytes = pair_rounds_smem_bytes(mn);
+  cudaFuncSetAttribute(k_pair_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, rbytes);
+  k_pair_rounds<<<s1 - s0, kRoundsNT, rbytes, st>>>(S, s0);
   ++nl;
   return nl;
 }

@@ -89,9 +89,10 @@ void launch_tc_prepare_q(Search* S, int s, int precision, cudaStream_t st) {
 }
 
 // BDT(i, k) = B(i, k) D(k) in the input format, through a shared-memory
-// transpose of 64 x 64 tiles (coalesced on both sides).
+// transpose of 64 x 64 tiles (coalesced on both sides); with with_bd the same
+// values also go to BD in FP64 (the eigendecomposition's B diag(D)).
 template <int KIND>
-__global__ void __launch_bounds__(256) k_tc_set_bdt(Search* S, TileMap tm, int force) {
+__global__ void __launch_bounds__(256) k_tc_set_bdt(Search* S, TileMap tm, int force, int with_bd) {
   __shared__ double tile[64][65];
   int t;
   const int si = find_search(tm, t);
@@ -102,7 +103,10 @@ __global__ void __launch_bounds__(256) k_tc_set_bdt(Search* S, TileMap tm, int f
   for (int e = threadIdx.x; e < 64 * 64; e += 256) {
     const int ii = e & 63, kk = e >> 6;
     const int i = i0 + ii, k = k0 + kk;
-    tile[kk][ii] = (i < n && k < n) ? s.B[i + static_cast<long long>(ldn) * k] * s.D[k] : 0.0;
+    const bool in = i < n && k < n;
+    const double v = in ? s.B[i + static_cast<long long>(ldn) * k] * s.D[k] : 0.0;
+    tile[kk][ii] = v;
+    if (with_bd && in) s.BD[i + static_cast<long long>(ldn) * k] = v;  // BD = B diag(D) in FP64
   }
   __syncthreads();
   ET<KIND>* bdt = static_cast<ET<KIND>*>(s.BDT);
@@ -115,8 +119,14 @@ __global__ void __launch_bounds__(256) k_tc_set_bdt(Search* S, TileMap tm, int f
 
 void launch_tc_set_bdt(Search* S, TileMap tm, int precision, int force, cudaStream_t st) {
   if (tm.total <= 0) return;
-  if (precision == 2) k_tc_set_bdt<1><<<tm.total, 256, 0, st>>>(S, tm, force);
-  else k_tc_set_bdt<0><<<tm.total, 256, 0, st>>>(S, tm, force);
+  if (precision == 2) k_tc_set_bdt<1><<<tm.total, 256, 0, st>>>(S, tm, force, 0);
+  else k_tc_set_bdt<0><<<tm.total, 256, 0, st>>>(S, tm, force, 0);
+}
+
+void launch_tc_set_bd_bdt(Search* S, TileMap tm, int precision, cudaStream_t st) {
+  if (tm.total <= 0) return;
+  if (precision == 2) k_tc_set_bdt<1><<<tm.total, 256, 0, st>>>(S, tm, 0, 1);
+  else k_tc_set_bdt<0><<<tm.total, 256, 0, st>>>(S, tm, 0, 1);
 }
 
 // -------------------------------- sampling ----------------------------------
