@@ -343,8 +343,20 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
 // FP32 cyclic Jacobi on A32 (from EH, symmetrised, shifted and scaled on
 // load). Rotations below FP32 resolution are skipped: a pair turns only when
 // a_pq^2 > 1e-12 |a_pp a_qq| and |a_pq| > 16 eps32 max|a_ii|.
-// FP32 arithmetic is cheap here, so a step costs its instruction count and
-// the length of its dependent chains:
+// A step is bound by its instruction count, so the matrix moves with the
+// round-robin ring instead of being addressed through it. Position (k, x)
+// is role x (a = 0: the pair's p, b = 1: its q) of pair k; at step r it
+// holds element p(r, k) or q(r, k). From step r to r + 1 the ring turns one
+// place: (k, a) -> (k - 1, a) for k >= 1, (0, a) -> (1, b), (k, b) ->
+// (k + 1, b) for 1 <= k <= P - 2, (P - 1, b) -> (P - 1, a), (0, b) stays.
+// The entry between positions (K, x) and (L, y), K < L, is kept in plane
+// 2x + y at K P + L; a diagonal block (K, K) keeps a_aa, a_ab, a_bb in planes
+// 0, 1, 3 at K P + K. A step reads each off-diagonal block of one buffer,
+// rotates it (two-sided, 16 FMAs), and writes its four entries to their
+// positions of the next step in the other buffer: all addresses are fixed
+// for the whole decomposition and held in registers, and consecutive lanes
+// (consecutive L) read and write consecutive words of each plane.
+// Further:
 //  - A32 is scaled by a power of two so that max|a_ij| <= 1: the scaling is
 //    exact, leaves the eigenvectors alone, and keeps the squares of the
 //    rotation test and of the angle away from overflow (and, for any spread
@@ -356,21 +368,18 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int st
 //    approximations; c = 1 / sqrt(1 + t^2) is rsqrtf plus one Newton step,
 //    s = t c. Any t gives an orthogonal (c, s); its last-bit error only
 //    leaves a_pq at FP32 rounding level, which the FP64 refinement removes;
-//  - only the upper triangle of A is kept (a_ij at min(i, j) + lda max(i, j));
-//  - the thread that computes a pair's rotation also updates its 2 x 2
-//    diagonal block (no other thread reads those three entries in the step);
-//  - each thread owns the same off-diagonal 2 x 2 blocks (pair Pi rows, pair
-//    Qi columns, Pi < Qi) in every step, their indices held in registers;
-//  - a step after a rotating one costs one barrier: the owner of the block
-//    that holds a pair's next pivot forms that pair's next rotation right
-//    after its own update (the diagonal entries it needs were written in the
-//    step before), so the rotations of step r + 1 are ready when the updates
-//    of step r are; after a quiet step the rotations come from A directly;
-//  - a pair's step record is one float4 (c, s, p | rotates << 16, q);
-//  - with n odd the padding row and column N - 1 are zero, their pairs never
-//    rotate (c = 1, s = 0), and the block updates keep them exactly zero, so
-//    no update tests an index against n;
-//  - the rotation count of a step is the barrier's own count.
+//  - the pivot of next-step pair k lands in the diagonal block (k, k) from
+//    exactly one block of the current step: (0, 1) for k = 0, (0, 2) for
+//    k = 1, (k - 1, k + 1) for 2 <= k <= P - 2, (P - 2, P - 1) for k = P - 1.
+//    The thread owning it forms the next rotation right after its own update
+//    (the diagonal entries it needs were finished in the step before) and
+//    writes the next diagonal block: one barrier per step. These P role
+//    blocks come first in the thread list, so the rotation arithmetic stays
+//    in the first warps, and their threads own no other block;
+//  - a step without rotations still turns the ring (its blocks only move);
+//  - with n odd the padding element N - 1 is the fixed (0, b): pair 0 never
+//    rotates and the padding row and column stay exactly zero;
+//  - a pair's step record is (c, s); (1, 0) when it does not rotate.
 // The eigenvectors are not formed here: each step that rotates anything
 // appends its (c, s) table to the rotation log, and k_jlog_apply replays the
 // log on the rows of V32 = I across the GPU.
@@ -395,6 +404,25 @@ __device__ __forceinline__ void j32_rotation(float app, float aqq, float apq, fl
   s = t * y;
 }
 
+// ring position (K, x) at step r + 1 of the position (K, x) at step r
+__device__ __forceinline__ void ring_next(int K, int x, int P, int& Kn, int& xn) {
+  if (x == 0) {
+    Kn = K >= 1 ? K - 1 : 1;
+    xn = K >= 1 ? 0 : 1;
+  } else {
+    Kn = (K == 0) ? 0 : (K == P - 1 ? P - 1 : K + 1);
+    xn = (K == P - 1) ? 0 : 1;
+  }
+}
+
+// offset (plane * P^2 + slot) of the entry between positions (K, x), (L, y)
+__device__ __forceinline__ int ring_offset(int K, int x, int L, int y, int P) {
+  const int PP = P * P;
+  if (K < L) return (2 * x + y) * PP + K * P + L;
+  if (K > L) return (2 * y + x) * PP + L * P + K;
+  return (x == y ? 3 * x : 1) * PP + K * P + K;
+}
+
 // off-diagonal 2 x 2 blocks per thread at the largest size: one for every
 // thread, then the rest of P (P - 1) / 2 over the kJ32NT - P threads that
 // form no rotation
@@ -409,11 +437,11 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   constexpr int NW = kJ32NT / 32;
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
-  const int lda = N + 1;            // odd: the 2 x 2 block accesses spread over the banks
+  const int PP = P * P;
   const int nblk = P * (P - 1) / 2;
-  float4* rinfo = reinterpret_cast<float4*>(fsm);          // 2 x P step records
-  float* A = fsm + 8 * P;
-  auto up = [=](int i, int j) -> float& { return i < j ? A[i + lda * j] : A[j + lda * i]; };
+  const bool pad = n & 1;  // pair 0 holds the padding element and never rotates
+  float2* rec = reinterpret_cast<float2*>(fsm);  // 2 x P step records (c, s)
+  float* buf = fsm + 4 * P;                       // 2 buffers x 4 planes x P^2
   // A32 = 2^-k (B^T C B - c I) rounded to FP32, with c the mean eigenvalue
   // (the trace over n, in FP64) and 2^k the power of two at or above
   // max a_ii. B^T C B is positive semi-definite, so |a_ij| <= max a_ii and
@@ -422,7 +450,9 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   // of the spectrum around c, which is where nearly equal eigenvalues of an
   // early descent (C close to a multiple of I) live. EH is exactly symmetric
   // (the product writes both triangles), so it is read once, a warp per
-  // column with the column's loads issued together.
+  // column with the column's loads issued together, each entry stored at
+  // its ring position of step 0: element 0 at (0, a), N - 1 at (0, b),
+  // 1 <= e <= P - 1 at (e, a), P <= e <= N - 2 at (N - 1 - e, b).
   const long long L = s.ldn;
   const double* A64 = s.EH;
   double tr = 0.0, dmax = 0.0;
@@ -437,135 +467,163 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   int ex = 0;
   if (dmax > 0.0) frexp(dmax, &ex);  // dmax = m 2^ex, m in [0.5, 1)
   const double scale = ldexp(1.0, -ex);
+  const int M = N - 1;
+  auto pos0 = [=](int e, int& K, int& x) {
+    if (e == 0) { K = 0; x = 0; }
+    else if (e == M) { K = 0; x = 1; }
+    else if (e <= P - 1) { K = e; x = 0; }
+    else { K = M - e; x = 1; }
+  };
   constexpr int kRow = (kE32Max + 31) / 32;
   for (int j = warp; j < N; j += NW) {
-    double x[kRow];
+    double v[kRow];
 #pragma unroll
     for (int u = 0; u < kRow; ++u) {
       const int i = lane + 32 * u;
-      x[u] = (i < n && j < n) ? A64[i + L * j] : 0.0;
+      v[u] = (i < n && j < n) ? A64[i + L * j] : 0.0;
     }
+    int Kj, xj;
+    pos0(j, Kj, xj);
 #pragma unroll
     for (int u = 0; u < kRow; ++u) {
       const int i = lane + 32 * u;
-      if (i < N) A[i + lda * j] = (i < n && j < n) ? static_cast<float>((x[u] - (i == j ? c : 0.0)) * scale) : 0.f;
+      if (i >= N) continue;
+      int Ki, xi;
+      pos0(i, Ki, xi);
+      // each unordered entry once: the upper block, or the diagonal block's a_aa, a_ab, a_bb
+      if (Ki < Kj || (Ki == Kj && xi <= xj))
+        buf[ring_offset(Ki, xi, Kj, xj, P)] =
+            (i < n && j < n) ? static_cast<float>((v[u] - (i == j ? c : 0.0)) * scale) : 0.f;
     }
   }
   __syncthreads();
   if (warp == 0) {
     float m = 0.f;
-    for (int i = lane; i < n; i += 32) m = fmaxf(m, fabsf(A[i + lda * i]));
+    for (int K = lane; K < P; K += 32) m = fmaxf(m, fmaxf(fabsf(buf[K * P + K]), fabsf(buf[3 * PP + K * P + K])));
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
     if (lane == 0) sh_amax = m;
   }
   __syncthreads();
-  // Each thread owns the same off-diagonal blocks (Pi, Qi), Pi < Qi, in every
+  // Each thread owns the same off-diagonal blocks (K, L), K < L, in every
   // step: entry tid of a list, and entries kJ32NT + (kJ32NT - P)(u - 1) +
-  // tid - P for u >= 1 when tid >= P (the threads that form rotations own one
-  // block). The list starts with the P role
-  // blocks, block k holding after its update the pivot of pair k of the next
-  // step, followed by the other blocks column by column. From step r to
-  // r + 1 the round-robin pair pi takes the p of pair pi + 1 and the q of
-  // pair pi - 1 (pair 0: the p of pair 1 and the fixed N - 1; pair 1: the p
-  // of pair 0; pair P - 1: the q of pairs P - 1 and P - 2), so the role
-  // blocks are (0, 1), (0, 2), (pi - 1, pi + 1) and (P - 2, P - 1), with the
-  // pivot at entry (q1, p2), (p1, p2), (q1, p2) and (q1, q2) for the block's
-  // row pair (p1, q1) and column pair (p2, q2). Putting them first keeps the
-  // rotation arithmetic of a step in the first warps, without divergence.
-  // bPQ: Pi | Qi << 16 (-1: none); brole: np | entry << 8, entry 0, 2, 3 =
-  // (p1, p2), (q1, p2), (q1, q2) (-1: none).
-  int bPQ[kJ32Blocks], brole[kJ32Blocks];
+  // tid - P for u >= 1 when tid >= P. The list starts with the P role blocks
+  // (block k holds the pivot of next-step pair k), then the others row by row
+  // (K ascending, L ascending). bKL: K | L << 8 (-1: none); bdst: the four
+  // entries' next offsets, (a, a) | (a, b) << 16 and (b, a) | (b, b) << 16.
+  int bKL[kJ32Blocks], bdst[kJ32Blocks][2];
 #pragma unroll
   for (int u = 0; u < kJ32Blocks; ++u) {
     const int k = u == 0 ? tid : (tid >= P ? kJ32NT + (kJ32NT - P) * (u - 1) + tid - P : nblk);
-    int Pi = 0, Qi = 0, ro = -1;
+    int K = 0, Lb = 0;
     if (k < P) {
-      if (k == 0) { Pi = 0; Qi = 1; ro = 0 | (2 << 8); }
-      else if (k == 1) { Pi = 0; Qi = 2; ro = 1 | (0 << 8); }
-      else if (k == P - 1) { Pi = P - 2; Qi = P - 1; ro = (P - 1) | (3 << 8); }
-      else { Pi = k - 1; Qi = k + 1; ro = k | (2 << 8); }
+      if (k == 0) { K = 0; Lb = 1; }
+      else if (k == 1) { K = 0; Lb = 2; }
+      else if (k == P - 1) { K = P - 2; Lb = P - 1; }
+      else { K = k - 1; Lb = k + 1; }
     } else if (k < nblk) {
-      // the (k - P)-th block that holds no pivot: column Qi has Qi blocks, of
-      // which (0, 1), (Qi - 2, Qi) and (P - 2, P - 1) hold one
+      // the (k - P)-th block that holds no pivot, row by row: row K has
+      // P - 1 - K blocks, of which (K, K + 2), (0, 1) and (P - 2, P - 1) hold one
       int j = k - P;
-      Qi = 1;
       for (;;) {
-        const int cnt = Qi - (Qi == 1) - (Qi >= 2) - (Qi == P - 1);
+        const int cnt = (P - 1 - K) - (K + 2 <= P - 1) - (K == 0) - (K == P - 2);
         if (j < cnt) break;
         j -= cnt;
-        ++Qi;
+        ++K;
       }
-      for (Pi = 0;; ++Pi) {
-        const bool role = (Qi == 1 && Pi == 0) || (Pi == Qi - 2) || (Qi == P - 1 && Pi == P - 2);
+      for (Lb = K + 1;; ++Lb) {
+        const bool role = (K == 0 && Lb == 1) || (Lb == K + 2) || (K == P - 2 && Lb == P - 1);
         if (role) continue;
         if (j == 0) break;
         --j;
       }
     }
-    bPQ[u] = k < nblk ? Pi | (Qi << 16) : -1;
-    brole[u] = ro;
+    bKL[u] = k < nblk ? K | (Lb << 8) : -1;
+    int d[4];
+#pragma unroll
+    for (int e = 0; e < 4; ++e) {
+      int Kn, xn, Ln, yn;
+      ring_next(K, e >> 1, P, Kn, xn);
+      ring_next(Lb, e & 1, P, Ln, yn);
+      d[e] = ring_offset(Kn, xn, Ln, yn, P);
+    }
+    bdst[u][0] = d[0] | (d[1] << 16);
+    bdst[u][1] = d[2] | (d[3] << 16);
+  }
+  // role of thread tid < P (its block is the list's entry tid): the entry
+  // holding the pivot of next pair k = tid (0: (a, a), 2: (b, a), 3: (b, b)),
+  // the current offsets of that pair's two diagonal entries, and the next
+  // offset of the current diagonal block k's off-diagonal entry
+  int r_ent = 0, r_srcA = 0, r_srcB = 0, r_move = 0;
+  if (tid < P) {
+    const int k = tid;
+    r_ent = k == 1 ? 0 : (k == P - 1 ? 3 : 2);
+    r_srcA = k <= P - 2 ? ring_offset(k + 1, 0, k + 1, 0, P) : ring_offset(P - 1, 1, P - 1, 1, P);
+    r_srcB = k >= 2 ? ring_offset(k - 1, 1, k - 1, 1, P) : ring_offset(0, k == 1 ? 0 : 1, 0, k == 1 ? 0 : 1, P);
+    int Ka, xa, Kb, xb;
+    ring_next(k, 0, P, Ka, xa);
+    ring_next(k, 1, P, Kb, xb);
+    r_move = ring_offset(Ka, xa, Kb, xb, P);
   }
   // below 16 eps32 max|a_ii| an off-diagonal entry is FP32 rounding noise
   const float floor_abs = 16.f * 1.1920929e-7f * sh_amax;
-  const int M = N - 1;
   const int cap = jlog_steps_cap(n);
   float2* jlog = reinterpret_cast<float2*>(s.jlog);
   int logged = 0;
-  // The rotation of pair np of step rn from A (its diagonal entries in A,
-  // its pivot apq given): applies the 2 x 2 diagonal block, stores the step
-  // record and the log entry (at the index the step gets if it rotates
-  // anything: later rotating steps overwrite the entries of a quiet one), and
-  // returns whether it rotates. The caller stores the pivot (zero if so).
-  auto rotate_pair = [&](int rn, int np, int pn, int qn, float apq, float4* rec) -> int {
+  // The rotation of pair k of step rn from its 2 x 2 diagonal block: the
+  // new diagonal entries, the step record, and the log entry (at the index
+  // the step gets if it rotates anything: later rotating steps overwrite the
+  // entries of a quiet one). Returns whether it rotates; apq becomes zero then.
+  auto rotate_pair = [&](int rn, int k, float& app, float& aqq, float& apq, float2* recn) -> int {
     float cr = 1.f, sr = 0.f;
     int act = 0;
-    if (pn < n && qn < n) {
-      const float app = A[pn + lda * pn], aqq = A[qn + lda * qn];
-      if (j32_rotates(app, aqq, apq, floor_abs)) {
-        float tn;
-        j32_rotation(app, aqq, apq, cr, sr, tn);
-        A[pn + lda * pn] = app - tn * apq;
-        A[qn + lda * qn] = aqq + tn * apq;
-        act = 1;
-      }
+    if (!(pad && k == 0) && j32_rotates(app, aqq, apq, floor_abs)) {
+      float tn;
+      j32_rotation(app, aqq, apq, cr, sr, tn);
+      app -= tn * apq;
+      aqq += tn * apq;
+      apq = 0.f;
+      act = 1;
     }
-    rec[np] = make_float4(cr, sr, __int_as_float(pn | (act << 16)), __int_as_float(qn));
+    recn[k] = make_float2(cr, sr);
     if (logged < cap) {
-      jlog[static_cast<size_t>(logged) * P + np] = make_float2(cr, sr);
-      if (np == 0) s.jlog_r[logged] = rn;
+      jlog[static_cast<size_t>(logged) * P + k] = make_float2(cr, sr);
+      if (k == 0) s.jlog_r[logged] = rn;
     }
     return act;
   };
-  // the rotations of step rn formed from A alone (the first step, and the
-  // step after a quiet one): pair tid
-  auto rotation_phase = [&](int rn, float4* rec) -> int {
-    int act = 0;
-    if (tid < P) {
-      const int p = (tid == 0) ? rn : (rn + tid) % M;
-      const int q = (tid == 0) ? M : (rn - tid + M) % M;
-      float& apq = up(p, q);
-      act = rotate_pair(rn, tid, p, q, apq, rec);
-      if (act) apq = 0.f;
-    }
-    return act;
-  };
-  auto rec = [=](int b) { return rinfo + b * P; };
+  // step 0: the rotations from the diagonal blocks of buffer 0
+  int act0 = 0;
+  if (tid < P) {
+    float app = buf[tid * P + tid], aqq = buf[3 * PP + tid * P + tid], apq = buf[PP + tid * P + tid];
+    act0 = rotate_pair(0, tid, app, aqq, apq, rec);
+    buf[tid * P + tid] = app;
+    buf[3 * PP + tid * P + tid] = aqq;
+    buf[PP + tid * P + tid] = apq;
+  }
+  int nact = __syncthreads_count(act0);
   int cur = 0, r = 0, sweep = 0, quiet = 0;
   bool converged = false;
-  int nact = __syncthreads_count(rotation_phase(0, rec(0)));
   while (true) {
-    // step r: its rotations are in rec(cur) (diagonal blocks applied)
+    // step r: its rotations are in the records of buffer cur (diagonal blocks applied)
+    const float* bc = buf + cur * 4 * PP;
     if (nact == 0) {
       // a quiet step: if no off-diagonal entry passes the test any more, the
       // remaining quiet steps of the window would change nothing
       ++quiet;
       if (quiet == 1 || (quiet & 15) == 0) {
         int pend = 0;
-        for (int Qi = warp; Qi < n && !pend; Qi += NW) {
-          const float aqq = A[Qi + lda * Qi];
-          for (int Pi = lane; Pi < Qi; Pi += 32)
-            pend |= j32_rotates(A[Pi + lda * Pi], aqq, A[Pi + lda * Qi], floor_abs);
+        for (int e = tid; e < PP && !pend; e += kJ32NT) {
+          const int K = e / P, Lb = e % P;
+          if (K > Lb) continue;
+          const float aK = bc[K * P + K], bK = bc[3 * PP + K * P + K];
+          if (K == Lb) {
+            pend |= j32_rotates(aK, bK, bc[PP + e], floor_abs);
+          } else {
+            const float aL = bc[Lb * P + Lb], bL = bc[3 * PP + Lb * P + Lb];
+            pend |= j32_rotates(aK, aL, bc[e], floor_abs) | j32_rotates(aK, bL, bc[PP + e], floor_abs) |
+                    j32_rotates(bK, aL, bc[2 * PP + e], floor_abs) | j32_rotates(bK, bL, bc[3 * PP + e], floor_abs);
+          }
         }
         if (!__syncthreads_or(pend)) quiet = M;
       }
@@ -579,53 +637,45 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
     }
     const int rn = (r + 1 == M) ? 0 : r + 1;
     if (rn == 0 && ++sweep == kJ32MaxSweeps) break;
+    // A <- J^T A J on the thread's blocks, each entry written to its position
+    // of step rn in the other buffer; the role threads form the rotations of
+    // step rn and write the next diagonal blocks
+    float* bn = buf + (cur ^ 1) * 4 * PP;
+    const float2* rc = rec + cur * P;
+    float2* rnx = rec + (cur ^ 1) * P;
     int act = 0;
-    if (nact == 0) {
-      act = rotation_phase(rn, rec(cur ^ 1));
-    } else {
-      // A <- J^T A J on the thread's off-diagonal blocks, and the rotations
-      // of step rn whose pivots these blocks hold
-      const float4* ri = rec(cur);
 #pragma unroll
-      for (int u = 0; u < kJ32Blocks; ++u) {
-        if (bPQ[u] < 0) continue;
-        const float4 iP = ri[bPQ[u] & 0xffff], iQ = ri[bPQ[u] >> 16];
-        const int wP = __float_as_int(iP.z), wQ = __float_as_int(iQ.z);
-        const bool rot = (wP | wQ) >> 16;
-        const int ro = brole[u];
-        if (!rot && ro < 0) continue;
-        const int p1 = wP & 0xffff, q1 = __float_as_int(iP.w), p2 = wQ & 0xffff, q2 = __float_as_int(iQ.w);
-        float& e00 = up(p1, p2);
-        float& e01 = up(p1, q2);
-        float& e10 = up(q1, p2);
-        float& e11 = up(q1, q2);
-        float x00 = e00, x01 = e01, x10 = e10, x11 = e11;
-        if (rot) {
-          const float cP = iP.x, sP = iP.y, cQ = iQ.x, sQ = iQ.y;
-          const float y00 = x00 * cQ - x01 * sQ, y01 = x00 * sQ + x01 * cQ;
-          const float y10 = x10 * cQ - x11 * sQ, y11 = x10 * sQ + x11 * cQ;
-          x00 = cP * y00 - sP * y10;
-          x01 = cP * y01 - sP * y11;
-          x10 = sP * y00 + cP * y10;
-          x11 = sP * y01 + cP * y11;
-        }
-        if (ro >= 0) {
-          const int ent = ro >> 8;
-          const int pn = ent == 3 ? q2 : p2, qn = ent == 0 ? p1 : q1;
-          const float apq = ent == 0 ? x00 : (ent == 2 ? x10 : x11);
-          const int a = rotate_pair(rn, ro & 0xff, pn, qn, apq, rec(cur ^ 1));
-          act |= a;
-          if (a) {
-            if (ent == 0) x00 = 0.f;
-            else if (ent == 2) x10 = 0.f;
-            else x11 = 0.f;
-          }
-        }
-        e00 = x00;
-        e01 = x01;
-        e10 = x10;
-        e11 = x11;
+    for (int u = 0; u < kJ32Blocks; ++u) {
+      if (bKL[u] < 0) continue;
+      const int K = bKL[u] & 0xff, Lb = bKL[u] >> 8;
+      const int o = K * P + Lb;
+      float x[4] = {bc[o], bc[PP + o], bc[2 * PP + o], bc[3 * PP + o]};
+      const float2 gK = rc[K], gL = rc[Lb];
+      if (gK.y != 0.f || gL.y != 0.f) {
+        const float cP = gK.x, sP = gK.y, cQ = gL.x, sQ = gL.y;
+        const float y00 = x[0] * cQ - x[1] * sQ, y01 = x[0] * sQ + x[1] * cQ;
+        const float y10 = x[2] * cQ - x[3] * sQ, y11 = x[2] * sQ + x[3] * cQ;
+        x[0] = cP * y00 - sP * y10;
+        x[1] = cP * y01 - sP * y11;
+        x[2] = sP * y00 + cP * y10;
+        x[3] = sP * y01 + cP * y11;
       }
+      if (u == 0 && tid < P) {
+        const int k = tid;
+        float app = bc[r_srcA], aqq = bc[r_srcB];
+        float apq = r_ent == 0 ? x[0] : (r_ent == 2 ? x[2] : x[3]);
+        act = rotate_pair(rn, k, app, aqq, apq, rnx);
+        if (r_ent == 0) x[0] = apq;
+        else if (r_ent == 2) x[2] = apq;
+        else x[3] = apq;
+        bn[k * P + k] = app;
+        bn[3 * PP + k * P + k] = aqq;
+        bn[r_move] = bc[PP + k * P + k];  // the current diagonal block's a_ab moves on
+      }
+      bn[bdst[u][0] & 0xffff] = x[0];
+      bn[bdst[u][0] >> 16] = x[1];
+      bn[bdst[u][1] & 0xffff] = x[2];
+      bn[bdst[u][1] >> 16] = x[3];
     }
     nact = __syncthreads_count(act);
     cur ^= 1;
@@ -639,7 +689,7 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
 
 int jacobi32_smem_bytes(int n) {
   const int N = n + (n & 1), P = N / 2;
-  return 2 * P * 16 + (N + 1) * N * 4;
+  return 2 * P * 8 + 2 * 4 * P * P * 4;
 }
 
 // V32 from the rotation log: row i of V32 = e_i^T J_1 J_2 ... J_T, and the
