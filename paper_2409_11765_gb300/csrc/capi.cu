@@ -9,6 +9,7 @@
 // decisions (restarts, lambda doubling, the lazy eigendecomposition cadence)
 // are taken on the device, so the host only enqueues work, and a whole-batch
 // generation replays one captured CUDA graph per phase.
+#include <algorithm>
 #include <cmath>
 #include <cstddef>
 #include <cstdarg>
@@ -49,6 +50,8 @@ struct cmaes_s {
   int max_n = 0, max_n_small_jacobi = 0, max_n_cluster_jacobi = 0, max_n_global_jacobi = 0;
   bool any_rotated = false, any_sphere = false;
   bool any_plain_eig = false;  // a search outside the refined eigensolver route (warm start B^T C B by k_eig_gemm_*)
+  int max_n_big = 0;           // largest n of the searches whose FP32 Jacobi runs over many CTAs
+  std::vector<Search> hs_probe;  // host copy of the searches, read between FP32 Jacobi sweeps
   long long launches = 0;
   // profiling
   bool profiling = false;
@@ -227,12 +230,59 @@ static void enqueue_cov(cmaes_t h, int s0, int s1, cudaStream_t st) {
   count_launch(h, kPhaseCov, t.total);
 }
 
+// The many-CTA FP32 Jacobi of the refined route (n > kEigMixedMaxN): one
+// launch per step over the large searches of [s0, s1). Once per sweep of the
+// largest of them the host reads the searches back and stops when each has
+// converged (a full quiet window after its last rotation) or spent its
+// budget. Needs the stream to be synchronisable: this phase is never captured
+// in a graph while such searches exist.
+static int enqueue_jacobi32_big(cmaes_t h, int s0, int s1, cudaStream_t st) {
+  TileMap tload = h->tiles(TK_JBLOAD, s0, s1), tblk = h->tiles(TK_JBBLK, s0, s1);
+  TileMap trows = h->tiles(TK_JBROWS, s0, s1);
+  if (tblk.total <= 0) return 0;
+  int nl = 3;
+  launch_j32b_start(h->dS, tload, s0, s1, st);
+  int Mmax = 0;
+  for (int s = s0; s < s1; ++s) {
+    const int n = h->hs[s].n;
+    if (eig_big_route(n)) Mmax = std::max(Mmax, n + (n & 1) - 1);
+  }
+  const int tcap = kJ32BigSweeps * Mmax;
+  h->hs_probe.resize(h->count);
+  for (int t = 0; t < tcap; ++t) {
+    if (t > 0 && t % 64 == 0) {  // ends the quiet window early once nothing is left to rotate
+      launch_j32b_check(h->dS, tblk, t, st);
+      ++nl;
+    }
+    launch_j32b_step(h->dS, tblk, t, st);
+    ++nl;
+    if ((t + 1) % Mmax == 0 && t + 1 < tcap) {
+      if (cudaMemcpyAsync(h->hs_probe.data() + s0, h->dS + s0, sizeof(Search) * (s1 - s0), cudaMemcpyDeviceToHost,
+                          st) != cudaSuccess ||
+          cudaStreamSynchronize(st) != cudaSuccess)
+        break;  // the sticky error surfaces at the next check
+      bool running = false;
+      for (int s = s0; s < s1 && !running; ++s) {
+        const Search& x = h->hs_probe[s];
+        if (x.done || !x.eig_due || !eig_big_route(x.n)) continue;
+        const int M = x.n + (x.n & 1) - 1;
+        running = !x.jb_conv && (t + 1 < x.jb_tmax) && (t + 1 - x.jb_last_act < M);
+      }
+      if (!running) break;
+    }
+  }
+  launch_jlog_big(h->dS, trows, h->max_n_big, st);
+  return nl + 1;
+}
+
 static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap sq = h->tiles(TK_SQUARE, s0, s1);
   {
     TileMap tfl = h->tiles(TK_FLAT, s0, s1);
     TileMap tsy = h->tiles(TK_FLATSYM, s0, s1);
-    const int nl = launch_eig_mixed(h->dS, tfl, tsy, s0, s1, h->max_n, st);
+    int nl = launch_eig_mixed_head(h->dS, tfl, tsy, s0, s1, h->max_n, st);
+    if (h->max_n_big > 0) nl += enqueue_jacobi32_big(h, s0, s1, st);
+    nl += launch_eig_mixed_tail(h->dS, tfl, tsy, s0, s1, h->max_n, st);
     h->launches += nl;
     h->phase_launch[kPhaseEig] += nl;
   }
@@ -312,6 +362,7 @@ static void drop_graphs(cmaes_t h) {
 static cmaes_status ensure_graphs(cmaes_t h) {
   if (h->graphs_ready) return CMAES_OK;
   for (int k = 0; k < kNumPhases; ++k) {
+    if (k == kPhaseEig && h->max_n_big > 0) continue;  // host-driven: enqueued directly
     const long long l0 = h->launches, p0 = h->phase_launch[k];
     cudaGraph_t g = nullptr;
     CUDA_TRY(h, cudaStreamBeginCapture(h->stream, cudaStreamCaptureModeRelaxed));
@@ -346,7 +397,7 @@ static cmaes_status enqueue_generation(cmaes_t h, int s0, int s1, cudaStream_t s
     if (rg != CMAES_OK) return rg;
   }
   auto run = [&](int k) -> cmaes_status {
-    if (!graphed) {
+    if (!graphed || (k == kPhaseEig && h->max_n_big > 0)) {
       enqueue_phase(h, k, s0, s1, st);
       return CMAES_OK;
     }
@@ -526,12 +577,17 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * jlog_pairs(n) * 8);  // jlog
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * 4);                  // jlog_r
     }
+    if (eig_big_route(n)) {
+      b += align256(jb_buf_floats(n) * 4);                         // jb_buf
+      b += align256(static_cast<size_t>(jlog_pairs(n)) * 16);      // jb_rec
+    }
     b += align256(lc * 8);                             // f
     b += 2 * align256(lc * 4);                         // order rank
     base[s] = total;
     total += b;
     if (n > h->max_n) h->max_n = n;
     if (!eig_refined_route(n)) h->any_plain_eig = true;
+    if (eig_big_route(n) && n > h->max_n_big) h->max_n_big = n;
     int* jm = n <= kJacobiSmallN ? &h->max_n_small_jacobi
               : n <= kJacobiClusterN ? &h->max_n_cluster_jacobi : &h->max_n_global_jacobi;
     if (n > *jm) *jm = n;
@@ -604,6 +660,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.jlog = reinterpret_cast<float*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * jlog_pairs(x.n) * 8));
       x.jlog_r = reinterpret_cast<int*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * 4));
     }
+    if (eig_big_route(x.n)) {
+      x.jb_buf = reinterpret_cast<float*>(take(jb_buf_floats(x.n) * 4));
+      x.jb_rec = reinterpret_cast<float*>(take(static_cast<size_t>(jlog_pairs(x.n)) * 16));
+    }
     if (h->mixed) {
       x.X = reinterpret_cast<double*>(take(ldn * lc * 8));
     } else {
@@ -649,6 +709,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_FLAT: t = eig_refined_route(x.n) ? tiles_flat(x.n) : 0; break;
         case TK_REEVAL: t = h->mixed ? tiles_reeval(x.n) : 0; break;
         case TK_FLATSYM: t = eig_refined_route(x.n) ? tiles_flat_sym(x.n) : 0; break;
+        case TK_JBBLK: t = tiles_jb_blocks(x.n); break;
+        case TK_JBLOAD: t = tiles_jb_load(x.n); break;
+        case TK_JBROWS: t = tiles_jb_rows(x.n); break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;

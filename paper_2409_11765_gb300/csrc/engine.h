@@ -67,6 +67,15 @@ struct Search {
   float *jlog;        // FP32 Jacobi rotation log: jlog_steps_cap(n) x jlog_pairs(n) (c, s) pairs
   int *jlog_r;        // jlog_steps_cap(n): round-robin step index r of each logged step
   int jlog_steps, jlog_pad_;  // logged steps of the last FP32 Jacobi
+  // many-CTA FP32 Jacobi (n > kEigMixedMaxN): two ring-layout buffers, two
+  // P-long (c, s) record arrays, the last step that rotated, the step budget,
+  // the rounding floor, and A32 = scale (A - shift I)
+  float *jb_buf, *jb_rec;
+  int jb_last_act, jb_tmax;
+  float jb_floor;
+  int jb_conv;           // converged: a whole-matrix check found nothing to rotate
+  int jb_pend, jb_done;  // that check's pending flag and CTA count
+  double jb_shift, jb_scale;
   int *err;           // device status word shared by the handle (bit 0: wait timed out)
 };
 
@@ -96,7 +105,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -123,17 +132,27 @@ void launch_eig_gemm_BtT(Search* S, TileMap tm, cudaStream_t st);
 // n <= kJacobiClusterN), one CTA per search on global memory (larger n).
 constexpr int kJacobiSmallN = 32;
 constexpr int kJacobiClusterN = 256;
-// Searches with kJacobiSmallN < n <= kEigMixedMaxN (any precision) take the
-// FP32-preconditioned, FP64-refined route of kernels_eig_mixed.cu.
+// Searches with kJacobiSmallN < n <= kEigBigMaxN (any precision) take the
+// FP32-preconditioned, FP64-refined route of kernels_eig_mixed.cu: its FP32
+// Jacobi runs in one CTA's shared memory up to kEigMixedMaxN
+// (kernels_eig_mixed.cu) and as one launch per step over many CTAs above it
+// (kernels_eig_big.cu). Larger n keep the plain warm-started FP64 Jacobi.
 constexpr int kEigMixedMaxN = 160;
-__host__ __device__ inline bool eig_refined_route(int n) { return n > kJacobiSmallN && n <= kEigMixedMaxN; }
+constexpr int kEigBigMaxN = 4096;
+__host__ __device__ inline bool eig_refined_route(int n) { return n > kJacobiSmallN && n <= kEigBigMaxN; }
 __host__ __device__ inline bool eig_refined_route(const Search& s) { return eig_refined_route(s.n); }
+__host__ __device__ inline bool eig_big_route(int n) { return n > kEigMixedMaxN && n <= kEigBigMaxN; }
 // The FP32 Jacobi of that route runs at most kJ32MaxSweeps sweeps of N - 1
-// round-robin steps (N = n rounded up to even) and logs the rotations of each
-// step that rotates anything: N / 2 (c, s) pairs, identity for idle pairs.
+// round-robin steps (N = n rounded up to even) in one CTA and logs the
+// rotations of each step that rotates anything; the many-CTA form runs at
+// most kJ32BigSweeps sweeps and logs every step. A logged step is N / 2
+// (c, s) pairs, identity for idle pairs.
 constexpr int kJ32MaxSweeps = 20;
+constexpr int kJ32BigSweeps = 16;
 __host__ __device__ inline int jlog_pairs(int n) { return (n + (n & 1)) / 2; }
-__host__ __device__ inline int jlog_steps_cap(int n) { return kJ32MaxSweeps * (n + (n & 1) - 1); }
+__host__ __device__ inline int jlog_steps_cap(int n) {
+  return (eig_big_route(n) ? kJ32BigSweeps : kJ32MaxSweeps) * (n + (n & 1) - 1);
+}
 void launch_jacobi_variant(Search* S, int s0, int s1, bool smem, int lo_n, int hi_n, int max_n,
                            cudaStream_t st);
 void launch_jacobi_cluster(Search* S, int s0, int s1, int lo_n, int hi_n, int layout_n, cudaStream_t st);
@@ -163,6 +182,19 @@ int tiles_flat(int n);
 __host__ __device__ inline int tiles_reeval(int n) { return (n + 31) / 32; }
 int tiles_flat_sym(int n);
 int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st);
+// the refined route in two parts around the many-CTA FP32 Jacobi: the
+// warm-start products (and the one-CTA FP32 Jacobi), then the refinement
+int launch_eig_mixed_head(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st);
+int launch_eig_mixed_tail(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st);
+// launchers (kernels_eig_big.cu)
+int tiles_jb_blocks(int n);
+int tiles_jb_load(int n);
+int tiles_jb_rows(int n);
+size_t jb_buf_floats(int n);
+void launch_j32b_start(Search* S, TileMap tload, int s0, int s1, cudaStream_t st);
+void launch_j32b_step(Search* S, TileMap tblk, int t, cudaStream_t st);
+void launch_j32b_check(Search* S, TileMap tblk, int t, cudaStream_t st);
+void launch_jlog_big(Search* S, TileMap trows, int max_n, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);

@@ -54,6 +54,8 @@ constexpr float kJ32Tol = 1e-6f;
 __device__ __forceinline__ bool mixed_route_due(const Search& s) {
   return !s.done && s.eig_due && eig_refined_route(s);
 }
+// the one-CTA FP32 Jacobi, its log replay and the shared-memory pair rounds
+__device__ __forceinline__ bool small_route_due(const Search& s) { return mixed_route_due(s) && s.n <= kE32Max; }
 
 // ---------------------------------------------------------------------------
 // FP64 products of the refinement: CTA t of a search computes outputs
@@ -433,7 +435,7 @@ __global__ void __launch_bounds__(kJ32NT, 1) k_jacobi32(Search* S, int s0) {
   extern __shared__ __align__(16) float fsm[];
   __shared__ float sh_amax;
   Search& s = S[s0 + blockIdx.x];
-  if (!mixed_route_due(s)) return;
+  if (!small_route_due(s)) return;
   constexpr int NW = kJ32NT / 32;
   const int n = s.n, N = n + (n & 1), P = N / 2, tid = threadIdx.x;
   const int lane = tid & 31, warp = tid >> 5;
@@ -834,7 +836,7 @@ __global__ void __launch_bounds__(kLogNT) k_jlog_apply(Search* S, int s0) {
   __shared__ float2 lcs[2][kLogChunkMax];
   __shared__ int lr[2][kLogStepsMax];
   const Search& s = S[s0 + blockIdx.y];
-  if (!mixed_route_due(s)) return;
+  if (!small_route_due(s)) return;
   const int n = s.n, N = n + (n & 1), P = N / 2;
   const int i0 = blockIdx.x * kLogRows;
   if (i0 >= n) return;
@@ -890,7 +892,7 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
   __shared__ double papp[kRoundsPick], paqq[kRoundsPick], papq[kRoundsPick];
   __shared__ double shr[kRoundsNT / 32];
   Search& s = S[s0 + blockIdx.x];
-  if (!mixed_route_due(s) || !s.mixed) return;
+  if (!small_route_due(s) || !s.mixed) return;
   const int n = s.n, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const long long L = s.ldn;
   double* Ag = s.EA;
@@ -1041,7 +1043,24 @@ __global__ void __launch_bounds__(kRoundsNT) k_pair_rounds(Search* S, int s0) {
 int pair_rounds_smem_bytes(int n) { return (n + 1) * n * 8; }
 
 
-int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
+int launch_eig_mixed_head(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
+  if (tflat.total <= 0 || s1 <= s0) return 0;
+  int nl = 0;
+  k_oa_gemm<<<tflat.total, kFW * 32, 0, st>>>(S, tflat, OA_W0);
+  k_oa_gemm<<<tsym.total, kFW * 32, 0, st>>>(S, tsym, OA_W1);  // symmetric result: upper triangle only
+  nl += 2;
+  if (max_n > kJacobiSmallN) {
+    const int mn = max_n < kE32Max ? max_n : kE32Max;
+    const int bytes = jacobi32_smem_bytes(mn);
+    cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+    k_jacobi32<<<s1 - s0, kJ32NT, bytes, st>>>(S, s0);
+    k_jlog_apply<<<dim3(ceil_div(mn, kLogRows), s1 - s0), kLogRows * 32, 0, st>>>(S, s0);
+    nl += 2;
+  }
+  return nl;
+}
+
+int launch_eig_mixed_tail(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
   if (tflat.total <= 0 || s1 <= s0) return 0;
   int nl = 0;
   const int gf = tflat.total, gs = tsym.total;
@@ -1053,14 +1072,6 @@ int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int
     k_oa_gemm<<<gs, kFW * 32, 0, st>>>(S, tsym, op);
     ++nl;
   };
-  flat(OA_W0);
-  sym(OA_W1);
-  const int mn = max_n < kE32Max ? max_n : kE32Max;
-  const int bytes = jacobi32_smem_bytes(mn);
-  cudaFuncSetAttribute(k_jacobi32, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-  k_jacobi32<<<s1 - s0, kJ32NT, bytes, st>>>(S, s0);
-  k_jlog_apply<<<dim3(ceil_div(mn, kLogRows), s1 - s0), kLogRows * 32, 0, st>>>(S, s0);
-  nl += 2;
   flat(OA_X0);
   for (int step = 0; step < 2; ++step) {
     flat(step == 0 ? OA_T0 : OA_T1);
@@ -1073,11 +1084,17 @@ int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int
   flat(OA_N2);
   flat(OA_T3);
   sym(OA_A);
+  const int mn = max_n < kE32Max ? max_n : kE32Max;
   const int rbytes = pair_rounds_smem_bytes(mn);
   cudaFuncSetAttribute(k_pair_rounds, cudaFuncAttributeMaxDynamicSharedMemorySize, rbytes);
   k_pair_rounds<<<s1 - s0, kRoundsNT, rbytes, st>>>(S, s0);
   ++nl;
   return nl;
+}
+
+int launch_eig_mixed(Search* S, TileMap tflat, TileMap tsym, int s0, int s1, int max_n, cudaStream_t st) {
+  return launch_eig_mixed_head(S, tflat, tsym, s0, s1, max_n, st) +
+         launch_eig_mixed_tail(S, tflat, tsym, s0, s1, max_n, st);
 }
 
 }  // namespace cmaes_gb300
