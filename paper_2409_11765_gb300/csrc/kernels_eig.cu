@@ -215,7 +215,10 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         // a quiet step: if no off-diagonal entry passes the test any more, the
         // rest of the quiet window would change nothing
         ++quiet;
-        if (quiet == 1 || quiet % (SMEM ? 16 : 256) == 0) {
+        // (on global memory a check reads all of A: at the 64th quiet step and
+        // every 256th after it, so that isolated rotating steps, as in a
+        // cleanup, do not each cost a pass over the matrix)
+        if (SMEM ? (quiet == 1 || quiet % 16 == 0) : (quiet == 64 || quiet % 256 == 0)) {
           int pend = 0;
           for (int j = tid >> 5; j < n && !pend; j += kJacobiNT / 32) {
             const double ajj = A[j + lda * j];
