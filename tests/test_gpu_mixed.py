@@ -52,7 +52,7 @@ def _grad_terms(kind, p, X):
 
 @pytest.mark.parametrize("prec", [1, 2])
 @pytest.mark.parametrize("n,lam,kind", [(10, 10, 1), (100, 544, 2), (65, 130, 1), (130, 300, 2),
-                                         (160, 320, 1)])
+                                         (160, 320, 1), (300, 300, 2)])
 def test_mixed_builtin_generation_sample_and_objective(prec, n, lam, kind):
     import paper_2409_11765_gb300 as eng
     from oracle import cmaes, objectives, philox

@@ -39,8 +39,9 @@ def _states(ns, stream0=0, cond=1e3):
     (130, 40, 1),     # cluster Jacobi
     (159, 30, 2),     # refined route, odd n: the padding pair of the FP32 Jacobi
     (160, 40, 1),     # largest refined-route size: four 2 x 2 blocks per FP32 Jacobi thread
-    (256, 30, 2),     # largest cluster-Jacobi size
-    (300, 40, 1),     # global-memory Jacobi
+    (161, 32, 2),     # smallest size of the many-CTA FP32 Jacobi, odd n
+    (256, 30, 2),     # largest cluster-Jacobi size (cleanup of the many-CTA route)
+    (300, 40, 1),     # global-memory Jacobi (cleanup of the many-CTA route)
 ])
 def test_teacher_forced_generation(n, lam, kind):
     gpu, ora = teacher_forced([n], [lam], [kind], _states([n]), eig_every=1)
