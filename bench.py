@@ -203,10 +203,10 @@ def eig_flops(n, decompositions):
 
 
 # DRAM bytes of the eigendecomposition phase per generation (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum over its kernels, one warm generation of the headline workload; see
-# profiles/eig_traffic_rastrigin-n100-kdist_tf32.md). Valid only for the engine sources it was
+# dram__bytes_write.sum over its kernels, one warm generation of the headline workload, one
+# capture). Valid only for the engine sources it was
 # measured on: any change to them makes the roofline's traffic null until it is measured again.
-EIG_TRAFFIC = {"bytes": 35937792, "sources_sha256_16": "1faf58cbfd277e16"}
+EIG_TRAFFIC = {"bytes": 36952064, "sources_sha256_16": "1e1b39f484888128"}
 
 
 def engine_sources_sha():

@@ -164,20 +164,12 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   }
   if (tid == 0) sh_rot = 0;
   __syncthreads();
-  // On the refined route (here n > kJacobiClusterN) A = X^T C X comes from FP64
-  // products whose rounding reaches n eps64 max|a_ii|. On mixed handles
-  // entries below four such bounds are not rotated (their contract is a
-  // backward error of 1e-12 relative to the FP32 covariance). FP64 handles
-  // keep the plain relative test: at these sizes the FP32 stage leaves pairs
-  // of close eigenvalues whose remains, stopped at a floor, would add up to
-  // more than the 1e-12 reconstruction error of the FP64 contract.
-  double floor_abs = 0.0;
-  if (eig_refined_route(s) && s.mixed) {
-    double am = 0.0;
-    for (int i = tid; i < n; i += kJacobiNT) am = fmax(am, fabs(A[i + lda * i]));
-    am = block_max<kJacobiNT>(am, shr);
-    floor_abs = 4.0 * n * 0x1p-53 * am;
-  }
+  // The plain relative test on every handle, also as the cleanup of the
+  // refined route (n > kJacobiClusterN here): at these sizes the FP32 stage
+  // leaves pairs of close eigenvalues whose remains, if stopped at a rounding
+  // floor of n eps64 max|a_ii|, add up to more than the 1e-12 reconstruction
+  // error of the contract.
+  const double floor_abs = 0.0;
 
   int sweeps = 0;
   // every pair meets once in any N - 1 consecutive steps, so N - 1 steps in a
