@@ -36,7 +36,7 @@ constexpr double kPdFloor = 1e-16;
 int jacobi_smem_bytes(int n, bool smem_mats) {
   const int N = n + (n & 1), P = N / 2;
   const int mats = smem_mats ? 2 * (N + 1) * N * 8 : 0;
-  return mats + P * (3 * 8 + 3 * 4) + N * (2 * 8 + 4) + 16;
+  return mats + P * (3 * 8 + 4 * 4) + N * (2 * 8 + 4) + 16;
 }
 
 int jacobi_smem_max_n() {
@@ -110,6 +110,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   extern __shared__ double dsm[];
   __shared__ double shr[32];
   __shared__ long long sh_rot;
+  __shared__ int sh_m;  // rotating pairs of the current step
   Search& s = S[s0 + blockIdx.x];
   if (s.done || !s.eig_due) return;
   const int n = s.n, ldn = s.ldn;
@@ -138,6 +139,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   int* rq = rp + P;
   int* ra = rq + P;
   int* rk = ra + P;
+  int* al = rk + N;  // the rotating pairs of a step, in no particular order
 
   // symmetrised A = (EA + EA^T) / 2; V = B
   if (SMEM) {
@@ -162,7 +164,10 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
       V[i + lda * j] = s.B[i + static_cast<long long>(ldn) * j];
     }
   }
-  if (tid == 0) sh_rot = 0;
+  if (tid == 0) {
+    sh_rot = 0;
+    sh_m = 0;
+  }
   __syncthreads();
   // The plain relative test on every handle, also as the cleanup of the
   // refined route (n > kJacobiClusterN here): at these sizes the FP32 stage
@@ -201,6 +206,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         if (act) {
           act_any = 1;
           atomicAdd(reinterpret_cast<unsigned long long*>(&sh_rot), 1ull);
+          al[atomicAdd(&sh_m, 1)] = i;
         }
       }
       if (__syncthreads_count(act_any) == 0) {
@@ -226,6 +232,56 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         continue;
       }
       quiet = 0;
+      const int m = sh_m;
+      if (!SMEM && 6LL * m * n < static_cast<long long>(P) * P) {
+        // Few rotations (as in a cleanup after the refinement): the m pairs'
+        // columns of A, then their rows, then their exact 2 x 2 blocks, then
+        // V's columns, O(m n) instead of a pass over every block. Pairs are
+        // disjoint, so each entry gets at most one column and one row
+        // rotation, in that order, whatever the order of the list.
+        double* pre = ev;  // free until the eigenvalues: a_pp, a_qq, a_pq before the step
+        for (int k = tid; k < m; k += kJacobiNT) {
+          const int i = al[k], p = rp[i], q = rq[i];
+          pre[3 * k] = A[p + lda * p];
+          pre[3 * k + 1] = A[q + lda * q];
+          pre[3 * k + 2] = A[p + lda * q];
+        }
+        __syncthreads();
+        for (long long e = tid; e < static_cast<long long>(m) * n; e += kJacobiNT) {  // A <- A J
+          const int k = static_cast<int>(e / n), r = static_cast<int>(e % n);
+          const int i = al[k], p = rp[i], q = rq[i];
+          const double c = rc[i], sn = rsn[i], x = A[r + lda * p], y = A[r + lda * q];
+          A[r + lda * p] = c * x - sn * y;
+          A[r + lda * q] = sn * x + c * y;
+        }
+        __syncthreads();
+        for (long long e = tid; e < static_cast<long long>(m) * n; e += kJacobiNT) {  // A <- J^T A
+          const int k = static_cast<int>(e / n), col = static_cast<int>(e % n);
+          const int i = al[k], p = rp[i], q = rq[i];
+          const double c = rc[i], sn = rsn[i], x = A[p + lda * col], y = A[q + lda * col];
+          A[p + lda * col] = c * x - sn * y;
+          A[q + lda * col] = sn * x + c * y;
+        }
+        __syncthreads();
+        for (int k = tid; k < m; k += kJacobiNT) {  // the exact 2 x 2 diagonal blocks
+          const int i = al[k], p = rp[i], q = rq[i];
+          const double t = rtn[i], app = pre[3 * k], aqq = pre[3 * k + 1], apq = pre[3 * k + 2];
+          A[p + lda * p] = app - t * apq;
+          A[q + lda * q] = aqq + t * apq;
+          A[p + lda * q] = 0.0;
+          A[q + lda * p] = 0.0;
+        }
+        for (long long e = tid; e < static_cast<long long>(m) * n; e += kJacobiNT) {  // V <- V J
+          const int k = static_cast<int>(e / n), row = static_cast<int>(e % n);
+          const int i = al[k], p = rp[i], q = rq[i];
+          const double c = rc[i], sn = rsn[i], vp = V[row + lda * p], vq = V[row + lda * q];
+          V[row + lda * p] = c * vp - sn * vq;
+          V[row + lda * q] = sn * vp + c * vq;
+        }
+        if (tid == 0) sh_m = 0;
+        __syncthreads();
+        continue;
+      }
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;
       for (int b = tid; b < nblk; b += kJacobiNT) {
@@ -273,6 +329,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
         V[row + lda * p] = c * vp - sn * vq;
         V[row + lda * q] = sn * vp + c * vq;
       }
+      if (tid == 0) sh_m = 0;
       __syncthreads();
     }
   }
