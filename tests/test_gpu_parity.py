@@ -61,6 +61,16 @@ def test_batch_of_uneven_searches():
         check_generation(gpu, ora)
 
 
+def test_batch_of_uneven_large_searches():
+    """Several searches on the many-CTA FP32 Jacobi (different n, so different
+    step counts per sweep) share its launches with a one-CTA-route search."""
+    ns, lams, kinds = [40, 170, 261], [20, 30, 24], [1, 2, 1]
+    states = _states(ns, 40)
+    for s in range(len(ns)):
+        gpu, ora = teacher_forced(ns, lams, kinds, states, search=s, eig_every=1)
+        check_generation(gpu, ora)
+
+
 def test_batch_invariance_bitwise():
     """A search gives bit-identical results alone and inside a batch."""
     import paper_2409_11765_gb300 as eng
