@@ -284,50 +284,104 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
       }
       // A <- J^T A J per 2x2 block (P <= Q), mirrored
       const int nblk = P * (P + 1) / 2;
-      for (int b = tid; b < nblk; b += kJacobiNT) {
-        // row-major enumeration of the upper triangle of the P x P block grid
+      // row-major enumeration of the upper triangle of the P x P block grid:
+      // b = Qi (Qi + 1) / 2 + Pi, Pi <= Qi
+      auto block_of = [](int b, int& Pi, int& Qi) {
         int bp = static_cast<int>((sqrtf(static_cast<float>(8 * b + 1)) - 1.0f) * 0.5f);
         while ((bp + 1) * (bp + 2) / 2 <= b) ++bp;
         while (bp * (bp + 1) / 2 > b) --bp;
-        // b = bp (bp + 1) / 2 + bq', map to (P_idx = bq', Q_idx = bp) with P_idx <= Q_idx
-        const int bq = b - bp * (bp + 1) / 2;
-        const int Pi = bq, Qi = bp;
-        const int aP = ra[Pi], aQ = ra[Qi];
-        if (!aP && !aQ) continue;
-        const int p1 = rp[Pi], q1 = rq[Pi], p2 = rp[Qi], q2 = rq[Qi];
-        if (Pi == Qi) {
-          const double app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
-          const double t = rtn[Pi];
-          A[p1 + lda * p1] = app - t * apq;
-          A[q1 + lda * q1] = aqq + t * apq;
-          A[p1 + lda * q1] = 0.0;
-          A[q1 + lda * p1] = 0.0;
-          continue;
+        Pi = b - bp * (bp + 1) / 2;
+        Qi = bp;
+      };
+      if (SMEM) {
+        for (int b = tid; b < nblk; b += kJacobiNT) {
+          int Pi, Qi;
+          block_of(b, Pi, Qi);
+          const int aP = ra[Pi], aQ = ra[Qi];
+          if (!aP && !aQ) continue;
+          const int p1 = rp[Pi], q1 = rq[Pi], p2 = rp[Qi], q2 = rq[Qi];
+          if (Pi == Qi) {
+            const double app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
+            const double t = rtn[Pi];
+            A[p1 + lda * p1] = app - t * apq;
+            A[q1 + lda * q1] = aqq + t * apq;
+            A[p1 + lda * q1] = 0.0;
+            A[q1 + lda * p1] = 0.0;
+            continue;
+          }
+          const double cP = rc[Pi], sP = rsn[Pi], cQ = rc[Qi], sQ = rsn[Qi];
+          const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
+          const double a = (vp1 && vp2) ? A[p1 + lda * p2] : 0.0;
+          const double bb = (vp1 && vq2) ? A[p1 + lda * q2] : 0.0;
+          const double c = (vq1 && vp2) ? A[q1 + lda * p2] : 0.0;
+          const double d = (vq1 && vq2) ? A[q1 + lda * q2] : 0.0;
+          const double y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
+          const double y10 = c * cQ - d * sQ, y11 = c * sQ + d * cQ;
+          const double x00 = cP * y00 - sP * y10, x01 = cP * y01 - sP * y11;
+          const double x10 = sP * y00 + cP * y10, x11 = sP * y01 + cP * y11;
+          if (vp1 && vp2) { A[p1 + lda * p2] = x00; A[p2 + lda * p1] = x00; }
+          if (vp1 && vq2) { A[p1 + lda * q2] = x01; A[q2 + lda * p1] = x01; }
+          if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
+          if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
         }
-        const double cP = rc[Pi], sP = rsn[Pi], cQ = rc[Qi], sQ = rsn[Qi];
-        const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
-        const double a = (vp1 && vp2) ? A[p1 + lda * p2] : 0.0;
-        const double bb = (vp1 && vq2) ? A[p1 + lda * q2] : 0.0;
-        const double c = (vq1 && vp2) ? A[q1 + lda * p2] : 0.0;
-        const double d = (vq1 && vq2) ? A[q1 + lda * q2] : 0.0;
-        const double y00 = a * cQ - bb * sQ, y01 = a * sQ + bb * cQ;
-        const double y10 = c * cQ - d * sQ, y11 = c * sQ + d * cQ;
-        const double x00 = cP * y00 - sP * y10, x01 = cP * y01 - sP * y11;
-        const double x10 = sP * y00 + cP * y10, x11 = sP * y01 + cP * y11;
-        if (vp1 && vp2) { A[p1 + lda * p2] = x00; A[p2 + lda * p1] = x00; }
-        if (vp1 && vq2) { A[p1 + lda * q2] = x01; A[q2 + lda * p1] = x01; }
-        if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
-        if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
-      }
-      // V <- V J for the active pairs
-      for (long long e = tid; e < static_cast<long long>(P) * n; e += kJacobiNT) {
-        const int pi = static_cast<int>(e / n), row = static_cast<int>(e % n);
-        if (!ra[pi]) continue;
-        const int p = rp[pi], q = rq[pi];
-        const double c = rc[pi], sn = rsn[pi];
-        const double vp = V[row + lda * p], vq = V[row + lda * q];
-        V[row + lda * p] = c * vp - sn * vq;
-        V[row + lda * q] = sn * vp + c * vq;
+        // V <- V J for the active pairs
+        for (long long e = tid; e < static_cast<long long>(P) * n; e += kJacobiNT) {
+          const int pi = static_cast<int>(e / n), row = static_cast<int>(e % n);
+          if (!ra[pi]) continue;
+          const int p = rp[pi], q = rq[pi];
+          const double c = rc[pi], sn = rsn[pi];
+          const double vp = V[row + lda * p], vq = V[row + lda * q];
+          V[row + lda * p] = c * vp - sn * vq;
+          V[row + lda * q] = sn * vp + c * vq;
+        }
+      } else {
+        // On global memory the step is driven by the list of its m rotating
+        // pairs: warp w takes pairs al[w], al[w + NW], ... and its lanes the
+        // partner pairs, so only the blocks with a rotating pair are visited
+        // (each once: a block of two rotating pairs belongs to the lower
+        // one), and V's rows follow the same pairs. No integer division and
+        // no pass over idle blocks, whatever m is.
+        constexpr int NW = kJacobiNT / 32;
+        const int lane = tid & 31, warp = tid >> 5;
+        for (int k = warp; k < m; k += NW) {
+          const int a = al[k];
+          for (int j = lane; j < P; j += 32) {
+            if (ra[j] && j < a) continue;  // that block is pair j's
+            const int Pi = j < a ? j : a, Qi = j < a ? a : j;
+            const int p1 = rp[Pi], q1 = rq[Pi], p2 = rp[Qi], q2 = rq[Qi];
+            if (Pi == Qi) {  // the pair's own 2 x 2 block, set exactly
+              const double app = A[p1 + lda * p1], aqq = A[q1 + lda * q1], apq = A[p1 + lda * q1];
+              const double t = rtn[Pi];
+              A[p1 + lda * p1] = app - t * apq;
+              A[q1 + lda * q1] = aqq + t * apq;
+              A[p1 + lda * q1] = 0.0;
+              A[q1 + lda * p1] = 0.0;
+              continue;
+            }
+            const double cP = rc[Pi], sP = rsn[Pi], cQ = rc[Qi], sQ = rsn[Qi];
+            const bool vp1 = p1 < n, vq1 = q1 < n, vp2 = p2 < n, vq2 = q2 < n;
+            const double x0 = (vp1 && vp2) ? A[p1 + lda * p2] : 0.0;
+            const double x1 = (vp1 && vq2) ? A[p1 + lda * q2] : 0.0;
+            const double x2 = (vq1 && vp2) ? A[q1 + lda * p2] : 0.0;
+            const double x3 = (vq1 && vq2) ? A[q1 + lda * q2] : 0.0;
+            const double y00 = x0 * cQ - x1 * sQ, y01 = x0 * sQ + x1 * cQ;
+            const double y10 = x2 * cQ - x3 * sQ, y11 = x2 * sQ + x3 * cQ;
+            const double x00 = cP * y00 - sP * y10, x01 = cP * y01 - sP * y11;
+            const double x10 = sP * y00 + cP * y10, x11 = sP * y01 + cP * y11;
+            if (vp1 && vp2) { A[p1 + lda * p2] = x00; A[p2 + lda * p1] = x00; }
+            if (vp1 && vq2) { A[p1 + lda * q2] = x01; A[q2 + lda * p1] = x01; }
+            if (vq1 && vp2) { A[q1 + lda * p2] = x10; A[p2 + lda * q1] = x10; }
+            if (vq1 && vq2) { A[q1 + lda * q2] = x11; A[q2 + lda * q1] = x11; }
+          }
+          // V <- V J for pair a: its two columns, lanes over the rows
+          const int p = rp[a], q = rq[a];
+          const double c = rc[a], sn = rsn[a];
+          for (int row = lane; row < n; row += 32) {
+            const double vp = V[row + lda * p], vq = V[row + lda * q];
+            V[row + lda * p] = c * vp - sn * vq;
+            V[row + lda * q] = sn * vp + c * vq;
+          }
+        }
       }
       if (tid == 0) sh_m = 0;
       __syncthreads();
