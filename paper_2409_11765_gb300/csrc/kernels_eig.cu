@@ -22,7 +22,11 @@
 //      in ascending eigenvalue order (ties by index) and each column's entry of
 //      largest magnitude (first on ties) positive.
 // Small n keeps A and B in shared memory (one CTA per search); larger n runs
-// the same steps on the global-memory copies.
+// the same steps on the global-memory copies. For 32 < n <= kEigBigMaxN the
+// warm start and most of the work belong to the refined route
+// (kernels_eig_mixed.cu, kernels_eig_big.cu), and the global-memory variant
+// (n > kJacobiClusterN) is its cleanup: it starts from A = X^T C X, nearly
+// diagonal, and drives each step by the list of the pairs that rotate.
 #include <cmath>
 #include "device_common.cuh"
 

@@ -1,6 +1,8 @@
 // kernels_eig_mixed.cu -- mixed-precision route of the warm-started
-// eigendecomposition (32 < n <= 160, every handle precision: the FP32 work
-// only supplies the starting basis, the result is FP64-accurate).
+// eigendecomposition (32 < n <= kEigBigMaxN, every handle precision: the FP32
+// work only supplies the starting basis, the result is FP64-accurate). The
+// FP32 Jacobi here runs in one CTA (n <= kEigMixedMaxN); above that size it is
+// the many-CTA form of kernels_eig_big.cu, and the rest is shared.
 //
 // The FP64 Jacobi of kernels_eig.cu / kernels_jacobi_cluster.cu needs about
 // seven sweeps per decomposition when C moves a lot between generations, and on
@@ -64,8 +66,8 @@ __device__ __forceinline__ bool small_route_due(const Search& s) { return mixed_
 // its leading dimension (consecutive lanes, consecutive rows), the right one is
 // shared by the lanes of a column. FP64 issues at 1/64 of the FP32 rate, so
 // batches of loaded operands and independent accumulators keep the pipe busy
-// without staging the operands in shared memory; they stay in L1 / L2
-// (n <= 160).
+// without staging the operands in shared memory; they stay in L1 / L2 up to
+// n ~ 1000 (above it the products stream from L2 and HBM).
 // ---------------------------------------------------------------------------
 constexpr int kFW = 4;               // warps per CTA
 constexpr int kFP = 2;               // outputs per lane
@@ -308,7 +310,9 @@ __global__ void __launch_bounds__(kFW * 32) k_oa_gemm(Search* S, TileMap tm, int
 // orthogonality half -g_ij / 2. The bound keeps the second-order loss of
 // orthogonality of a step, sum_k |e_ki e_kj| <= n 2^-20, small enough that the
 // second step and the Newton-Schulz step bring X^T X to I within rounding
-// (1.5 (n 2^-20)^4 << eps64 for n <= 160).
+// (1.5 (n 2^-20)^4 << eps64 for n <= 160; at larger n only near neighbours in
+// the spectrum reach the bound, and what the refinement leaves goes to the
+// cleanup Jacobi).
 constexpr double kOaSep = 0x1p-10;
 __global__ void __launch_bounds__(kFW * 32) k_oa_e(Search* S, TileMap tm, int step) {
   int t;
