@@ -245,8 +245,8 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches,
 
 /* Work done by the eigensolver of search s since creation: decompositions,
  * FP64 Jacobi sweeps, plane rotations applied by them, and the FP32 Jacobi
- * sweeps that precondition them on mixed-precision handles (zero on FP64
- * handles). Any pointer may be NULL. Synchronises. */
+ * sweeps that precede them on the refined route (32 < n <= 4096, every handle
+ * precision; zero for other n). Any pointer may be NULL. Synchronises. */
 cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions,
                              long long* sweeps, long long* rotations,
                              long long* sweeps32);
