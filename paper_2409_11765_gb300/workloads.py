@@ -142,21 +142,32 @@ def ellipsoid_n1000(seed=SEED):
                     -4.0, 4.0, 1e-8, 0, False, 5000)
 
 
-def batch256(seed=SEED, count=256):
-    """Batched concurrent IPOP: n in {50,200,500,1000,2000} drawn from the seed,
-    lambda = (4 + floor(3 ln n)) 2^k with k ~ U{0..8}; objectives alternate
-    rotated ellipsoid (cond 1e6) and rotated Rastrigin by search index."""
+def batch256_shapes(seed=SEED, count=256):
+    """(n, lambda, objective kind) of every search of the 256-search batch:
+    n in {50,200,500,1000,2000} drawn from the seed, lambda = (4 + floor(3 ln
+    n)) 2^k with k ~ U{0..8}; objectives alternate rotated ellipsoid and
+    rotated Rastrigin by search index."""
     rng = rng_for(seed, 3, 0)
     dims = [50, 200, 500, 1000, 2000]
-    searches = []
+    shapes = []
     for s in range(count):
         n = int(dims[rng.integers(0, len(dims))])
         k = int(rng.integers(0, 9))
-        kind = ELLIPSOID if s % 2 == 0 else RASTRIGIN
+        shapes.append((n, default_lambda(n) << k, ELLIPSOID if s % 2 == 0 else RASTRIGIN))
+    return shapes
+
+
+def batch256(seed=SEED, count=256):
+    """Batched concurrent IPOP: the shapes of batch256_shapes, ellipsoids with
+    cond 1e6, x0 ~ U[-4,4]^n, sigma0 = 2. Every search restarts at its own
+    population size when it stops (the K-Distributed layout of §3.2.3: the
+    levels k = 0..8 already run side by side)."""
+    searches = []
+    for s, (n, lam, kind) in enumerate(batch256_shapes(seed, count)):
         prob = make_problem(kind, n, seed, 1000 + s, cond=1e6)
-        searches.append(SearchSpec(n, default_lambda(n) << k, 2.0,
-                                   start_point(n, -4.0, 4.0, seed, 1000 + s), prob))
-    return Workload("batch256-n50..2000", searches, -4.0, 4.0, 1e-8, 8, True, 0)
+        searches.append(SearchSpec(n, lam, 2.0, start_point(n, -4.0, 4.0, seed, 1000 + s), prob))
+    return Workload("batch256-n50..2000", searches, -4.0, 4.0, 1e-8, 255, False, 0,
+                    notes="K-Distributed: 256 searches of uneven (n, lambda) in one batch")
 
 
 def ellipsoid_n4096(seed=SEED, kind=ELLIPSOID):

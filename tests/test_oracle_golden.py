@@ -49,3 +49,26 @@ def test_n2_generation_file():
     for k, v in (("m", st.m), ("ps", st.ps), ("pc", st.pc), ("C", st.C.ravel())):
         assert np.allclose(v, num(k), atol=tol), k
     assert np.allclose(np.linalg.eigvalsh(st.C), num("eig"), atol=tol)
+
+
+def test_params_branches_file():
+    """d_sigma on both sides of its max(0, .) branch, MaxIter and the
+    TolHistFun history length against values worked out by hand."""
+    rows = _lines("params_branches.txt")
+    kinds = {r[0] for r in rows}
+    assert kinds == {"dsigma", "maxiter", "histlen"}
+    active = 0
+    for r in rows:
+        n, lam = int(r[1]), int(r[2])
+        p = Params(n, lam)
+        if r[0] == "dsigma":
+            mueff, cs, inner, ds = (float(x) for x in r[3:7])
+            assert abs(p.mueff - mueff) <= 5e-14 * mueff
+            assert abs(p.cs - cs) <= 5e-14
+            assert abs(p.ds - ds) <= 5e-14 * ds
+            active += inner > 0
+        elif r[0] == "maxiter":
+            assert p.max_iter == int(r[3])
+        else:
+            assert p.hist_len == int(r[3])
+    assert active == 2
