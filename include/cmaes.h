@@ -18,6 +18,16 @@
  *   - Every call returns a cmaes_status; none throws, aborts or exits.
  *   - A CUDA error is sticky: once a call returns CMAES_ECUDA, every later call
  *     on that handle returns CMAES_ECUDA (cmaes_last_error() gives the text).
+ *     So is a device wait that gave up: every device wait (tensor-core
+ *     mbarriers) is bounded, and one that runs out records it in the handle's
+ *     device status word; the next call that reads that word (cmaes_sync and
+ *     every call that synchronises) and every later call return
+ *     CMAES_ETIMEOUT.
+ *   - NaN / infinite objective values are accepted and ranked last. When a
+ *     search's state itself becomes non-finite (m, sigma or diag C), its stop
+ *     test (CMAES_STOP_NONFINITE) restarts or ends that search, and the next
+ *     call that reads the device status word returns CMAES_ENUMERIC once; the
+ *     handle stays usable.
  *   - Host arrays passed in are copied before the call returns; the caller
  *     keeps ownership. Host arrays passed out are caller-allocated and sized as
  *     documented. Matrices are n x n, column-major, leading dimension n.
@@ -278,14 +288,26 @@ long long cmaes_kernel_launches(cmaes_t h);
  * kernels overlap on the GPU (different streams, or different threads on the
  * same device) race and give wrong results. Nothing in it needs to start at
  * zero. The first call on each device looks up the array's device address
- * (cudaGetSymbolAddress, with that device current); make that first call
- * before any stream capture. The call is asynchronous on `stream`; errors:
+ * (cudaGetSymbolAddress, with that device current) and keeps it for the life
+ * of the process; make that first call before any stream capture. A reset of
+ * the device or of its primary context (cudaDeviceReset) reloads the module
+ * and leaves the kept address stale: do not call this entry point after such
+ * a reset. The call is asynchronous on `stream`; errors:
  * EINVAL (arguments, size), ECUDA; the text is in cmaes_last_error(NULL). */
 cmaes_status cmaes_evaluate_noalloc(int kind, int n, int lambda, const double* X,
                                     int ld, const double* Q, int ldq,
                                     const double* lambda_diag,
                                     const double* xstar, double* f,
                                     void* stream);
+
+/* Fault injection from the host (no counterpart in the paper; for tests of
+ * the error paths above, which must not be provoked by faulting the GPU):
+ * waits for the handle's stream, then ORs `bits` into the handle's device
+ * status word exactly as the device does. bits: 1 = a bounded device wait
+ * timed out (later calls return CMAES_ETIMEOUT, sticky), 2 = a search's state
+ * became non-finite (the next status read returns CMAES_ENUMERIC once). Other
+ * bits: EINVAL. */
+cmaes_status cmaes_inject_status(cmaes_t h, int bits);
 
 const char* cmaes_strerror(cmaes_status st);
 /* Text of the last error on h (or of the last failed create if h is NULL). */

@@ -22,7 +22,7 @@ __all__ = [
     "cmaes_get_state", "cmaes_set_state", "cmaes_get_generation", "cmaes_query",
     "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
     "cmaes_ask_async", "cmaes_tell_async",
-    "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_strerror",
+    "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_inject_status", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
 
@@ -107,6 +107,7 @@ def lib():
         "cmaes_evaluate_noalloc": (I, [I, I, I, V, I, V, I, V, V, V, V]),
         "cmaes_ask_async": (I, [H, I, I, ctypes.POINTER(V), ctypes.POINTER(ctypes.c_int), V]),
         "cmaes_tell_async": (I, [H, I, I, ctypes.POINTER(V), V]),
+        "cmaes_inject_status": (I, [H, I]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
         "cmaes_destroy": (None, [H]),
@@ -342,6 +343,12 @@ def cmaes_evaluate_noalloc(kind, n, lam, X_ptr, ld, Q_ptr, ldq, lamdiag_ptr, xst
     st = lib().cmaes_evaluate_noalloc(kind, n, lam, X_ptr, ld, Q_ptr, ldq, lamdiag_ptr, xstar_ptr,
                                       f_ptr, stream)
     _check(None, st)
+
+
+def cmaes_inject_status(h, bits):
+    """ORs bits into the handle's device status word (host-side fault
+    injection; see include/cmaes.h)."""
+    _check(h, lib().cmaes_inject_status(h, bits))
 
 
 def cmaes_strerror(st):

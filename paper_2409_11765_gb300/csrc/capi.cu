@@ -126,10 +126,23 @@ static cmaes_status launch_check(cmaes_t h, const char* what) {
   return CMAES_OK;
 }
 
+// Reads the device status word (the handle's stream must be idle). A timed-out
+// wait makes the handle unusable (sticky CMAES_ETIMEOUT); a non-finite state
+// is reported once as CMAES_ENUMERIC and its bit cleared, since the stop test
+// already restarted or ended the search.
 static cmaes_status check_device_status(cmaes_t h) {
   int e = 0;
   CUDA_TRY(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
-  if (e & 1) return set_error(h, CMAES_ETIMEOUT, "a tensor-core wait timed out on the device");
+  if (e & kDevErrTimeout) {
+    h->err = CMAES_ETIMEOUT;
+    h->msg = "a bounded device wait timed out";
+    return CMAES_ETIMEOUT;
+  }
+  if (e & kDevErrNonFinite) {
+    const int cleared = e & ~kDevErrNonFinite;
+    CUDA_TRY(h, cudaMemcpy(h->d_err, &cleared, sizeof(int), cudaMemcpyHostToDevice));
+    return set_error(h, CMAES_ENUMERIC, "a search's state became non-finite; the search was restarted or ended");
+  }
   return CMAES_OK;
 }
 
@@ -808,6 +821,18 @@ cmaes_status cmaes_step_batch(cmaes_t h, int generations, void* stream) {
     CUDA_TRY(h, cudaStreamWaitEvent(h->stream, ev, 0));
     CUDA_TRY(h, cudaEventDestroy(ev));
   }
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_inject_status(cmaes_t h, int bits) {
+  CHECK_HANDLE(h);
+  if (bits & ~(kDevErrTimeout | kDevErrNonFinite))
+    return set_error(h, CMAES_EINVAL, "unknown status bits 0x%x", bits);
+  CUDA_TRY(h, cudaStreamSynchronize(h->stream));
+  int e = 0;
+  CUDA_TRY(h, cudaMemcpy(&e, h->d_err, sizeof(int), cudaMemcpyDeviceToHost));
+  e |= bits;
+  CUDA_TRY(h, cudaMemcpy(h->d_err, &e, sizeof(int), cudaMemcpyHostToDevice));
   return CMAES_OK;
 }
 

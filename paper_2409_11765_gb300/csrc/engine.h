@@ -35,6 +35,12 @@ struct DevOptions {
 
 // Per-search descriptor, resident in device memory. Constant part first,
 // then the scalars that the kernels update every generation.
+// Bits of the device status word (Search::err): a bounded device wait gave up
+// (reported as CMAES_ETIMEOUT, sticky), a search's state became non-finite
+// (reported once as CMAES_ENUMERIC; the stop test restarts or ends the search).
+constexpr int kDevErrTimeout = 1;
+constexpr int kDevErrNonFinite = 2;
+
 struct Search {
   // --- constant after create ---
   int n, ldn, lam0, lam_cap, mu_cap, hist_cap, index, obj;
@@ -76,7 +82,7 @@ struct Search {
   int jb_conv;           // converged: a whole-matrix check found nothing to rotate
   int jb_pend, jb_done;  // that check's pending flag and CTA count
   double jb_shift, jb_scale;
-  int *err;           // device status word shared by the handle (bit 0: wait timed out)
+  int *err;           // device status word shared by the handle (kDevErr* bits)
 };
 
 // Flattened tiles of one kernel over a contiguous range of searches:

@@ -696,7 +696,10 @@ __global__ void __launch_bounds__(256) k_stop(Search* S, int s0, DevOptions o) {
     if (__dmul_rn(dmax, dmax) > __dmul_rn(__dmul_rn(o.cond_max, dmin), dmin)) flags |= 16;
     if (!any_axis_moves) flags |= 32;
     if (any_coord_stuck) flags |= 64;
-    if (any_nonfinite || !isfinite(sigma)) flags |= 128;
+    if (any_nonfinite || !isfinite(sigma)) {
+      flags |= 128;
+      atomicOr(s.err, kDevErrNonFinite);  // reported to the host as CMAES_ENUMERIC
+    }
     flags &= o.stop_mask;
     s.flags = flags;
     shi[0] = flags;

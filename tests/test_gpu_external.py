@@ -63,3 +63,43 @@ def test_async_argument_checks():
             eng.cmaes_ask_async(h, 2, 1, [buf.ctypes.data], buf.ctypes.data)  # empty range
     finally:
         eng.cmaes_destroy(h)
+
+
+def test_async_groups_follow_the_oracle():
+    """The asynchronous path against the oracle: every search starts from a
+    teacher-forced state with distinct eigenvalues, the host evaluates f with
+    the oracle's objectives, and after each generation every search's state
+    matches the oracle's generation fed the same points' values."""
+    import paper_2409_11765_gb300 as eng
+    from oracle import cmaes, objectives
+    from paper_2409_11765_gb300 import workloads as W
+    from paper_2409_11765_gb300.external import AsyncAskTell
+    from parity_util import oracle_state, rel, state_dict
+    ns, lams = [12, 7, 33], [10, 9, 40]
+    kinds = [W.ELLIPSOID, W.SPHERE, W.RASTRIGIN]
+    opt = eng.cmaes_default_options(precision=0, eig_every=1, max_restarts=0)
+    states = [W.random_state(n, SEED, 600 + i, cond=1e2) for i, n in enumerate(ns)]
+    probs = [W.make_problem(k, n, SEED, 50 + i, cond=1e3) for i, (n, k) in enumerate(zip(ns, kinds))]
+    h = eng.cmaes_create_batch(ns, lams, [d["m"] for d in states], [1.0] * 3, SEED, opt)
+    fns = [lambda X, p=p: objectives.evaluate(p.kind, X, p.Q, p.lamdiag, p.xstar) for p in probs]
+    orc = [oracle_state(d, n, lam, 1.0, gen=1) for d, n, lam in zip(states, ns, lams)]
+    opts = cmaes.Options(eig_every=1, max_restarts=0)
+    try:
+        for i, p in enumerate(probs):
+            eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
+            eng.cmaes_set_state(h, i, state_dict(states[i], ns[i], lams[i], gen=1))
+        pipe = AsyncAskTell(h, ns, lams, [(2, 3), (0, 2)])
+        for g in range(4):
+            pipe.run(fns, 1)
+            for i in range(3):
+                cmaes.generation(orc[i], SEED, i, cmaes.Problem(probs[i].kind, probs[i].xstar,
+                                                                probs[i].Q, probs[i].lamdiag), opts)
+                s = eng.cmaes_get_state(h, i, ns[i])
+                tol = 1e-12 * 10 ** (g / 5)
+                assert s["gen"] == orc[i].gen
+                assert rel(s["m"], orc[i].m) < tol, (g, i, rel(s["m"], orc[i].m))
+                assert rel(s["C"], orc[i].C) < tol, (g, i)
+                assert abs(s["sigma"] / orc[i].sigma - 1) < tol
+                assert abs(s["best_f"] - orc[i].best_f) <= tol * max(1.0, abs(orc[i].best_f))
+    finally:
+        eng.cmaes_destroy(h)
