@@ -1,20 +1,26 @@
 #!/usr/bin/env python3
 """Throughput of the batched CMA-ES generation loop on GB300.
 
-Workload (default): the IPOP-CMA-ES configuration on the rotated Rastrigin,
-n = 100, lambda0 = 17 with population levels 17 * 2^k for k = 0..9 (lambda up
-to 8704), laid out as the paper's K-Distributed strategy (§3.2.3): the ten
-levels run side by side as one batch of ten searches, each restarting at its
-own size when a stop test fires. One step = one generation of every search =
-17391 candidates sampled, evaluated and used in the update (rank,
-recombination, paths, step size, rank-one + rank-mu covariance update), plus
-the lazy FP64 eigendecomposition when due (every generation here) and the
+Workload (default, `batch256`): 256 concurrent IPOP-CMA-ES searches of uneven
+size in one batch: n drawn from {50, 200, 500, 1000, 2000}, lambda = (4 +
+floor(3 ln n)) 2^k with k drawn from 0..8, objectives alternating between a
+rotated ellipsoid (cond 1e6) and a rotated Rastrigin; every search restarts at
+its own population size when a stop test fires (the K-Distributed layout of
+§3.2.3, where all population levels run side by side). One step = one
+generation of every search = 264,864 candidates sampled, evaluated and used in
+the update (rank, recombination, paths, step size, rank-one + rank-mu
+covariance update), plus the lazy FP64 eigendecomposition where due and the
 stop tests. Inputs are seeded synthetic instances (no BBOB data).
 
 Prints one JSON line (rank 0). Timing: W warm-up generations, then K timed
 generations, each bracketed by CUDA events on the launch stream, with a
-256 MiB write between timed generations to flush L2. Per-phase device times
-come from CUDA events the engine records on the same stream.
+256 MiB write between timed generations to flush L2. The per-phase and
+per-kernel-stage device times come from a separate profiled handle that runs
+the same generations (the timed handle runs without profiling); `e2e` is a
+third handle, again over the same generations, timed on the host through the
+public API (cmaes_step_batch, then every search's best point and value read
+back with cmaes_best), with the same L2 flush between steps (outside the
+timed region).
 
 --impl reference times the FP64 CPU oracle on this host's cores on the same
 workload (test infrastructure; it is the method's plain restatement).
@@ -35,19 +41,27 @@ if ROOT not in sys.path:
 
 METRIC = "candidates/sec sampled+evaluated+updated; mixed vs plain FP64 GPU; % roofline"
 UNIT = "candidates/s"
+SEED = 20240918
+WORKLOADS = ("batch256", "rastrigin-n100-kdist", "ellipsoid-n1000", "ellipsoid-n4096",
+             "ellipsoid-n10", "rastrigin-n100-ipop")
 
 
 def parse_args():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=200)
-    ap.add_argument("--warmup", type=int, default=5)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["engine", "reference"], default="engine")
+    ap.add_argument("--workload", choices=WORKLOADS, default="batch256")
     ap.add_argument("--precision", choices=["fp64", "tf32", "bf16"], default="tf32",
-                    help="headline path; the other two are measured beside it")
-    ap.add_argument("--headline-only", action="store_true")
-    ap.add_argument("--e2e-steps", type=int, default=50)
-    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+                    help="headline path; the plain FP64 path is measured beside it")
+    ap.add_argument("--paths", default="fp64",
+                    help="comma-separated other precisions measured beside the headline ('' for none)")
+    ap.add_argument("--eig-method", choices=["auto", "jacobi", "tridiagonal"], default="auto")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extra", action="store_true",
+                    help="skip the extra n = 100 K-Distributed line")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     return ap.parse_args()
 
@@ -57,23 +71,39 @@ def dist_env():
     return D.env()
 
 
-def workload():
+def workload(name):
     from paper_2409_11765_gb300 import workloads as W
-    return W.rastrigin_n100_ipop(concurrent=True)
+    if name == "batch256":
+        return W.batch256()
+    if name == "rastrigin-n100-kdist":
+        return W.rastrigin_n100_ipop(concurrent=True)
+    if name == "rastrigin-n100-ipop":
+        return W.rastrigin_n100_ipop(concurrent=False)
+    if name == "ellipsoid-n1000":
+        return W.ellipsoid_n1000()
+    if name == "ellipsoid-n4096":
+        return W.ellipsoid_n4096()
+    return W.ellipsoid_n10()
 
 
-def workload_config(wl, precision):
-    s0 = wl.searches[0]
-    return {"workload": wl.name, "searches": len(wl.searches), "n": s0.n,
-            "lambdas": [s.lam for s in wl.searches],
+def workload_config(wl, precision, eig_method):
+    ns = sorted({s.n for s in wl.searches})
+    kinds = sorted({s.problem.kind for s in wl.searches})
+    names = {1: "rotated ellipsoid", 2: "rotated Rastrigin", 3: "sphere"}
+    return {"workload": wl.name, "searches": len(wl.searches), "n": ns,
+            "lambda_min": min(s.lam for s in wl.searches),
+            "lambda_max": max(s.lam for s in wl.searches),
             "candidates_per_step": wl.candidates_per_generation,
-            "objective": "rotated Rastrigin (seeded Haar Q, x* ~ U[-4,4]^n)",
-            "layout": "K-Distributed: levels lambda=17*2^k, k=0..9, one batch",
+            "objectives": [names[k] for k in kinds],
+            "restarts": "each search at its own lambda" if not wl.ipop_double else "lambda doubled",
             "precision": precision,
-            "gemms": {"fp64": "FP64 CUDA cores", "tf32": "tcgen05 kind::tf32 (objective, rank-mu: 3-term split)",
+            "gemms": {"fp64": "FP64 CUDA cores",
+                      "tf32": "tcgen05 kind::tf32 (objective, rank-mu: 3-term split)",
                       "bf16": "tcgen05 kind::f16 bf16 (objective, rank-mu: 3-term split)"}[precision],
-            "eig": "FP64 warm-started Jacobi, every generation (lazy rule gives 1)",
-            "l2": "256 MiB write between timed generations", "seed": 20240918}
+            "eig": "FP64, lazy cadence; " + {0: "tridiagonal route above n = 160, Jacobi route below",
+                                            1: "warm-started Jacobi route",
+                                            2: "Householder tridiagonal route"}[eig_method],
+            "l2": "256 MiB write between timed generations", "seed": SEED}
 
 
 # ----------------------------- CPU oracle ----------------------------------
@@ -90,56 +120,59 @@ def oracle_searches(wl):
     return sts, probs, opts
 
 
-def oracle_step(sts, probs, opts):
+def oracle_sample(wl, seconds):
+    """The oracle as it stands on this host's cores: generations of the batch's
+    searches in order (search by search) until `seconds` have passed.
+    Returns (candidates, searches done, generations, elapsed)."""
     from oracle import cmaes
-    from paper_2409_11765_gb300 import workloads as W
-    cand = 0
-    for i, (st, pr) in enumerate(zip(sts, probs)):
-        if not st.done:
-            cand += st.lam
-            cmaes.generation(st, W.SEED, i, pr, opts)
-    return cand
-
-
-def cpu_baseline(wl, seconds):
-    """The oracle as it stands, on this host's cores, for a bounded sample of
-    generations of the same batch."""
     sts, probs, opts = oracle_searches(wl)
     t0 = time.perf_counter()
     cand = 0
     gens = 0
+    done_searches = 0
     while True:
-        cand += oracle_step(sts, probs, opts)
+        for i, (st, pr) in enumerate(zip(sts, probs)):
+            if not st.done:
+                cand += st.lam
+                cmaes.generation(st, SEED, i, pr, opts)
+            if gens == 0:
+                done_searches = i + 1
+            if time.perf_counter() - t0 >= seconds:
+                return cand, done_searches, gens + (1 if done_searches == len(sts) else 0), \
+                    time.perf_counter() - t0
         gens += 1
-        el = time.perf_counter() - t0
-        if el >= seconds and gens >= 2:
-            break
+
+
+def cpu_baseline(wl, seconds):
+    cand, ns, gens, el = oracle_sample(wl, seconds)
     return {"value": cand / el, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
-            "sample": "%d generations of the full 10-search batch (%d candidates) in %.1f s; "
-                      "numpy FP64, BLAS threads = host cores" % (gens, cand, el)}
+            "sample": "%d candidates of the batch's first generations in %.1f s (%d of %d searches "
+                      "of generation 0 done%s); numpy FP64, BLAS threads = host cores"
+                      % (cand, el, ns, len(wl.searches),
+                         ", %d full generations" % gens if gens else "")}
 
 
 def run_reference(args):
     rank, _, world = dist_env()
     if rank != 0:
         return
-    wl = workload()
-    sts, probs, opts = oracle_searches(wl)
-    for _ in range(args.warmup):
-        oracle_step(sts, probs, opts)
-    t0 = time.perf_counter()
-    cand = 0
+    wl = workload(args.workload)
+    per_step = max(args.cpu_seconds / max(args.steps, 1), 1.0)
+    times, cands = [], []
     for _ in range(args.steps):
-        cand += oracle_step(sts, probs, opts)
-    el = time.perf_counter() - t0
-    value = cand / el
+        cand, _, _, el = oracle_sample(wl, per_step)
+        times.append(el)
+        cands.append(cand)
+    value = sum(cands) / sum(times)
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 0,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * el / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(times) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
-            "data": "synthetic", "config": workload_config(wl, "fp64"),
+            "data": "synthetic", "config": workload_config(wl, "fp64", 0),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": os.cpu_count(),
                              "kind": "oracle",
-                             "sample": "%d timed generations of the full batch" % args.steps},
+                             "sample": "each step: the batch's searches in order for %.1f s "
+                                       "(%d candidates per step on average)"
+                                       % (per_step, sum(cands) // max(len(cands), 1))},
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
@@ -192,21 +225,14 @@ class ClockSampler:
 
 
 # ------------------------------ GPU engine ----------------------------------
-def eig_flops(n, decompositions):
-    """Algorithmic FP64 flops of the eigendecompositions: per decomposition of
-    an n x n C warm-started from the previous basis, 4 n^3 for B^T C B, 9 n^3
-    per Jacobi sweep with s = 2 sweeps (a warm start needs one to three) and
-    2 n^3 for the basis update B V: 24 n^3. The figure is the problem's, not
-    the engine's: its refined route spends its FP64 flops on dense products
-    and its sweeps in FP32 (cmaes_eig_stats reports what actually ran)."""
-    return (4.0 + 9.0 * 2 + 2.0) * n ** 3 * decompositions
+PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
+DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
 
-
-# DRAM bytes of the eigendecomposition phase per generation (ncu dram__bytes_read.sum +
-# dram__bytes_write.sum over its kernels, one warm generation of the headline workload, one
-# capture). Valid only for the engine sources it was
-# measured on: any change to them makes the roofline's traffic null until it is measured again.
-EIG_TRAFFIC = {"bytes": 36944896, "sources_sha256_16": "6040ce6c27b78da5"}
+# DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
+# for the engine sources it was measured on (a SHA-256 of the CUDA sources
+# without comments): after any change to them the roofline's traffic is null
+# until it is measured again. Empty until a capture of the current sources.
+KERNEL_TRAFFIC = {}
 
 
 def engine_sources_sha():
@@ -230,55 +256,51 @@ def engine_sources_sha():
     return h.hexdigest()[:16]
 
 
-PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
-DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
+def make_handle(wl, prec, eig_method, rank):
+    import paper_2409_11765_gb300 as eng
+    from paper_2409_11765_gb300 import dist as D
+    opt = eng.cmaes_default_options(precision=PREC[prec], f_target=wl.f_target,
+                                    box_lo=wl.box_lo, box_hi=wl.box_hi,
+                                    max_restarts=min(wl.max_restarts, 255),
+                                    ipop_double=1 if wl.ipop_double else 0, eig_method=eig_method)
+    h = eng.cmaes_create_batch([s.n for s in wl.searches], [s.lam for s in wl.searches],
+                               [s.x0 for s in wl.searches], [s.sigma0 for s in wl.searches],
+                               D.rank_seed(SEED, rank), opt)
+    for i, s in enumerate(wl.searches):
+        p = s.problem
+        eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
+    return h
 
 
-def phase_flops(wl, prec_name, eig):
-    """Algorithmic work per step of each phase (flops), for the roofline."""
-    n = wl.searches[0].n
-    count = len(wl.searches)
-    lam_sum = wl.candidates_per_generation
-    mu_sum = sum(s.lam // 2 for s in wl.searches)
-    split = 1 if prec_name == "fp64" else 3   # split operands: three products
-    return {
-        "sample": 2.0 * lam_sum * n * n,
-        "objective": 2.0 * lam_sum * n * n * split,
-        "cov": (1.0 * mu_sum * n * (n + 1)) * split + 3.0 * count * n * n,
-        "eig": eig,
-        "update": 2.0 * count * n * n + 4.0 * mu_sum * n,
-        "stop": 0.0,
-    }
+def decomposition_work(eng, h, wl, before):
+    """Decompositions of each dimension done since `before` (cmaes_eig_stats)."""
+    out = {}
+    for i, s in enumerate(wl.searches):
+        k = eng.cmaes_eig_stats(h, i)["decompositions"] - before[i]
+        if k:
+            out[s.n] = out.get(s.n, 0) + k
+    return out
 
 
-def measure(args, prec_name, world, rank, dist, want_clocks):
+def measure(args, wl, prec, world, rank, dist, want_clocks, eig_method):
     import torch
     import paper_2409_11765_gb300 as eng
-    wl = workload()
-    count = len(wl.searches)
-    opt = eng.cmaes_default_options(precision=PREC[prec_name], f_target=wl.f_target,
-                                    box_lo=wl.box_lo, box_hi=wl.box_hi, max_restarts=255,
-                                    ipop_double=0)
-    ns = [s.n for s in wl.searches]
     from paper_2409_11765_gb300 import dist as D
-    h = eng.cmaes_create_batch(ns, [s.lam for s in wl.searches], [s.x0 for s in wl.searches],
-                               [s.sigma0 for s in wl.searches], D.rank_seed(20240918, rank), opt)
+    count = len(wl.searches)
+    ns = [s.n for s in wl.searches]
+    stream = torch.cuda.Stream()
+    torch.cuda.set_stream(stream)
+    sptr = stream.cuda_stream
+    flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
+    res = {}
+
+    # 1. timed handle: device time of K generations, no profiling
+    h = make_handle(wl, prec, eig_method, rank)
     try:
-        for i, s in enumerate(wl.searches):
-            p = s.problem
-            eng.cmaes_set_problem(h, i, p.kind, p.Q, p.lamdiag, p.xstar)
-        # a dedicated stream: the engine launches on it and the CUDA events
-        # that time the steps are recorded on it
-        stream = torch.cuda.Stream()
-        torch.cuda.set_stream(stream)
-        sptr = stream.cuda_stream
-        flush = torch.empty(256 * 1024 * 1024, dtype=torch.uint8, device="cuda")
         for _ in range(args.warmup):
             eng.cmaes_step_batch(h, 1, sptr)
         torch.cuda.synchronize()
-        eig0 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
-        eng.cmaes_phase_times(h, reset=True)
-        eng.cmaes_set_profiling(h, True)
+        before = [eng.cmaes_eig_stats(h, i)["decompositions"] for i in range(count)]
         launches0 = eng.cmaes_kernel_launches(h)
         starts = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
         ends = [torch.cuda.Event(enable_timing=True) for _ in range(args.steps)]
@@ -300,42 +322,85 @@ def measure(args, prec_name, world, rank, dist, want_clocks):
         torch.cuda.synchronize()
         if dist is not None:
             dist.barrier()
-        clocks = sampler.stop() if sampler else None
-        launches = eng.cmaes_kernel_launches(h) - launches0
-        eng.cmaes_set_profiling(h, False)
-        phase_ms, _ = eng.cmaes_phase_times(h, reset=True)
-        total_ms = D.max_over_ranks(sum(a.elapsed_time(b) for a, b in zip(starts, ends)), dist,
-                                    device="cuda")
-        eig1 = [eng.cmaes_eig_stats(h, i) for i in range(count)]
-        dec = sum(b["decompositions"] - a["decompositions"] for a, b in zip(eig0, eig1))
-        rot = sum(b["rotations"] - a["rotations"] for a, b in zip(eig0, eig1))
-        swp = sum(b["sweeps"] - a["sweeps"] for a, b in zip(eig0, eig1))
-        swp32 = sum(b["sweeps32"] - a["sweeps32"] for a, b in zip(eig0, eig1))
-        torch.cuda.set_stream(torch.cuda.default_stream())
-        # e2e through the public API: one generation and a host read of every
-        # search's best point and value, synchronised each step
-        e2e_t0 = time.perf_counter()
-        for _ in range(args.e2e_steps):
-            eng.cmaes_step_batch(h, 1)
-            for i in range(count):
-                eng.cmaes_best(h, i, ns[i])
-        e2e_el = time.perf_counter() - e2e_t0
+        res["clocks"] = sampler.stop() if sampler else None
+        res["gpu_launches"] = int(eng.cmaes_kernel_launches(h) - launches0)
+        eng.cmaes_sync(h)
+        step_ms = [a.elapsed_time(b) for a, b in zip(starts, ends)]
+        total_ms = D.max_over_ranks(sum(step_ms), dist, device="cuda")
+        res["decompositions"] = decomposition_work(eng, h, wl, before)
     finally:
         eng.cmaes_destroy(h)
     cand = wl.candidates_per_generation
-    n = ns[0]
-    flops = phase_flops(wl, prec_name, eig_flops(n, dec) / args.steps)
-    return {
-        "value": D.whole_job_rate(cand, args.steps, world, total_ms),
-        "ms_per_step": total_ms / args.steps,
-        "phases_ms_per_step": {k: v / args.steps for k, v in phase_ms.items()},
-        "phase_flops_per_step": flops,
-        "gpu_launches": int(launches),
-        "eig_work": {"decompositions": dec, "sweeps": swp, "rotations": rot, "sweeps_fp32": swp32},
-        "e2e": {"value": cand * args.e2e_steps * world / e2e_el, "unit": UNIT,
-                "h2d_bytes_per_step": 0, "d2h_bytes_per_step": sum(8 * m + 8 for m in ns)},
-        "clocks": clocks,
-    }
+    res["value"] = D.whole_job_rate(cand, args.steps, world, total_ms)
+    res["ms_per_step"] = total_ms / args.steps
+    res["step_ms"] = step_ms
+
+    # 2. profiled handle: the same generations with per-phase and per-stage events
+    h = make_handle(wl, prec, eig_method, rank)
+    try:
+        for _ in range(args.warmup):
+            eng.cmaes_step_batch(h, 1, sptr)
+        torch.cuda.synchronize()
+        eng.cmaes_phase_times(h, reset=True)
+        eng.cmaes_eig_stage_times(h, reset=True)
+        eng.cmaes_set_profiling(h, True)
+        for k in range(args.steps):
+            flush.fill_(k & 255)
+            eng.cmaes_step_batch(h, 1, sptr)
+        torch.cuda.synchronize()
+        phase_ms, _ = eng.cmaes_phase_times(h, reset=True)
+        stage_ms = eng.cmaes_eig_stage_times(h, reset=True)
+        eng.cmaes_set_profiling(h, False)
+    finally:
+        eng.cmaes_destroy(h)
+    res["phases_ms_per_step"] = {k: v / args.steps for k, v in phase_ms.items()}
+    res["eig_stages_ms_per_step"] = {k: v / args.steps for k, v in stage_ms.items()}
+
+    # 3. e2e handle: the same generations through the public API, host-timed
+    if not args.no_e2e:
+        h = make_handle(wl, prec, eig_method, rank)
+        try:
+            for _ in range(args.warmup):
+                eng.cmaes_step_batch(h, 1, sptr)
+            torch.cuda.synchronize()
+            el = 0.0
+            for k in range(args.steps):
+                flush.fill_(k & 255)
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                eng.cmaes_step_batch(h, 1, sptr)
+                for i in range(count):
+                    eng.cmaes_best(h, i, ns[i])
+                el += time.perf_counter() - t0
+        finally:
+            eng.cmaes_destroy(h)
+        res["e2e"] = {"value": cand * args.steps * world / el, "unit": UNIT,
+                      "h2d_bytes_per_step": 0, "d2h_bytes_per_step": sum(8 * m + 8 for m in ns)}
+    torch.cuda.set_stream(torch.cuda.default_stream())
+    del flush
+    torch.cuda.empty_cache()
+    return res
+
+
+def stage_flops(decomps):
+    """Algorithmic FP64 flops of the eigendecompositions per stage, from the
+    decompositions done: Householder reduction 4/3 n^3, back-transformation
+    2 n^3 (LAPACK's counts for dsytrd and dormtr); the eigenvalue and
+    eigenvector stages are O(n^2) per decomposition and the Newton-Schulz
+    orthogonalisation is not part of the minimal method (0)."""
+    red = sum(k * 4.0 / 3.0 * n ** 3 for n, k in decomps.items())
+    bt = sum(k * 2.0 * n ** 3 for n, k in decomps.items())
+    return {"reduction": red, "backtransform": bt, "eigenvalues": 0.0, "eigenvectors": 0.0,
+            "orthogonalisation": 0.0}
+
+
+def phase_flops(wl, prec):
+    """Algorithmic flops per step of the GEMM-shaped phases."""
+    split = 1 if prec == "fp64" else 3
+    samp = sum(2.0 * s.lam * s.n * s.n for s in wl.searches)
+    obj = sum(2.0 * s.lam * s.n * s.n for s in wl.searches if s.problem.kind != 3) * split
+    cov = sum((s.lam // 2) * s.n * (s.n + 1.0) for s in wl.searches) * split
+    return {"sample": samp, "objective": obj, "cov": cov}
 
 
 def run_engine(args):
@@ -352,57 +417,82 @@ def run_engine(args):
         _build.build()
     if dist is not None:
         dist.barrier()
-
+    eig_method = {"auto": 0, "jacobi": 1, "tridiagonal": 2}[args.eig_method]
+    wl = workload(args.workload)
     head = args.precision
-    runs = {head: measure(args, head, world, rank, dist, want_clocks=True)}
-    for other in ("fp64", "tf32", "bf16"):
-        if other != head and not args.headline_only:
-            runs[other] = measure(args, other, world, rank, dist, want_clocks=False)
+    runs = {head: measure(args, wl, head, world, rank, dist, True, eig_method)}
+    for other in [p for p in args.paths.split(",") if p]:
+        if other != head:
+            runs[other] = measure(args, wl, other, world, rank, dist, False, eig_method)
     r = runs[head]
+    extra = None
+    if not args.no_extra and args.workload != "rastrigin-n100-kdist":
+        wk = workload("rastrigin-n100-kdist")
+        a2 = argparse.Namespace(**vars(args))
+        a2.steps, a2.warmup, a2.no_e2e = 50, 5, True
+        x = measure(a2, wk, head, world, rank, dist, False, eig_method)
+        extra = {"workload": wk.name, "value": x["value"], "ms_per_step": x["ms_per_step"],
+                 "steps": a2.steps, "warmup": a2.warmup,
+                 "phases_ms_per_step": x["phases_ms_per_step"]}
 
-    # roofline of the dominant phase of the headline run
+    # roofline of the dominant kernel stage of the headline run
     fp64_peak = eng.probe_fma_tflops(64)
-    import json as _json
     peaks = {}
     try:
-        peaks = _json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+        peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
     except (OSError, ValueError):
         pass
-    dom = max(r["phases_ms_per_step"], key=r["phases_ms_per_step"].get)
-    dom_ms = r["phases_ms_per_step"][dom]
-    achieved = r["phase_flops_per_step"][dom] / (dom_ms * 1e-3) / 1e12
-    if dom in ("eig", "update", "stop") or head == "fp64":
-        bound, peak, src = "alu", fp64_peak, "FP64 DFMA probe measured live on this GPU"
+    steps = args.steps
+    cands = dict(r["eig_stages_ms_per_step"])
+    for k in ("sample", "objective", "update", "cov", "stop"):
+        cands[k] = r["phases_ms_per_step"][k]
+    eig_other = r["phases_ms_per_step"]["eig"] - sum(r["eig_stages_ms_per_step"].values())
+    cands["eig_other"] = max(eig_other, 0.0)
+    dom = max(cands, key=cands.get)
+    flops = stage_flops(r["decompositions"])
+    flops = {k: v / steps for k, v in flops.items()}
+    flops.update(phase_flops(wl, head))
+    dom_ms = cands[dom]
+    achieved = flops.get(dom, 0.0) / (dom_ms * 1e-3) / 1e12 if dom_ms > 0 else 0.0
+    if dom in ("reduction", "backtransform", "eigenvalues", "eigenvectors", "orthogonalisation",
+               "eig_other", "update", "stop") or head == "fp64":
+        bound, peak, src = "alu", fp64_peak, "FP64 FMA rate measured live by the engine's probe"
     else:
         bf16 = peaks.get("bf16_tflops", 1908.7)
         peak = bf16 * (0.5 if head == "tf32" else 1.0)
         bound, src = "tensor", ("MEASURED_PEAKS.json bf16 x nominal tf32/bf16 ratio 0.5"
                                 if head == "tf32" else "MEASURED_PEAKS.json bf16")
     traffic = None
-    if dom == "eig" and head != "fp64" and engine_sources_sha() == EIG_TRAFFIC["sources_sha256_16"]:
-        traffic = EIG_TRAFFIC["bytes"]
+    kt = KERNEL_TRAFFIC.get(dom)
+    if kt and engine_sources_sha() == kt["sources_sha256_16"]:
+        traffic = kt["bytes_per_step"]
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                "frac": achieved / peak, "traffic": traffic, "kernel": dom, "peak_source": src,
-                "algorithmic_flops_per_step": r["phase_flops_per_step"][dom]}
+                "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": dom,
+                "peak_source": src, "algorithmic_flops_per_step": flops.get(dom, 0.0),
+                "kernel_ms_per_step": dom_ms}
     if rank != 0:
         if dist is not None:
             dist.destroy_process_group()
         return
-    wl = workload()
     line = {"metric": METRIC, "value": r["value"], "unit": UNIT, "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": r["ms_per_step"],
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": DTYPE[head], "data": "synthetic", "config": workload_config(wl, head),
-            "roofline": roofline, "e2e": r["e2e"], "gpu_launches": r["gpu_launches"],
+            "dtype": DTYPE[head], "data": "synthetic", "config": workload_config(wl, head, eig_method),
+            "roofline": roofline, "e2e": r.get("e2e"), "gpu_launches": r["gpu_launches"],
             "clocks": r["clocks"], "phases_ms_per_step": r["phases_ms_per_step"],
-            "eig_ms_per_step": r["phases_ms_per_step"]["eig"], "eig_work": r["eig_work"]}
+            "eig_stages_ms_per_step": r["eig_stages_ms_per_step"],
+            "decompositions_per_step": {str(n): k / steps for n, k in sorted(r["decompositions"].items())},
+            "step_ms": r["step_ms"]}
     for other, o in runs.items():
         if other != head:
             line[other + "_path"] = {"value": o["value"], "ms_per_step": o["ms_per_step"],
                                      "phases_ms_per_step": o["phases_ms_per_step"],
-                                     "eig_work": o["eig_work"]}
-    if "fp64_path" in line:
+                                     "eig_stages_ms_per_step": o["eig_stages_ms_per_step"],
+                                     "e2e": o.get("e2e")}
+    if "fp64_path" in line and head != "fp64":
         line["mixed_over_fp64"] = r["value"] / line["fp64_path"]["value"]
+    if extra:
+        line["kdist_n100"] = extra
     if not args.no_cpu_baseline and world == 1:
         line["cpu_baseline"] = cpu_baseline(wl, args.cpu_seconds)
     print(json.dumps(line), flush=True)

@@ -90,6 +90,24 @@ typedef enum {
 #define CMAES_STOP_NONFINITE 128    /* m, sigma or diag C not finite           */
 #define CMAES_STOP_ALL 255
 
+/* Eigensolver of C = B D^2 B^T for 32 < n <= 4096 (smaller n always use a
+ * one-CTA FP64 Jacobi; larger n a warm-started FP64 Jacobi on one CTA).
+ *   JACOBI: warm-started from the previous basis; cyclic Jacobi sweeps in
+ *     FP32, FP64 accuracy recovered by two Ogita-Aishima refinement steps
+ *     and a Newton-Schulz step, then an FP64 Jacobi cleanup.
+ *   TRIDIAGONAL: Householder reduction to tridiagonal form, the route of
+ *     LAPACK's dsyev that the paper calls (§3.1): bisection for the
+ *     eigenvalues, inverse iteration for the eigenvectors, Newton-Schulz
+ *     steps for orthogonality, all in FP64.
+ *   AUTO (default): JACOBI up to n = 160 (its FP32 sweeps fit one CTA's
+ *     shared memory and beat the reduction's n sequential FP64 steps there),
+ *     TRIDIAGONAL above (the Jacobi sweeps' n steps each then span the GPU). */
+typedef enum {
+    CMAES_EIG_AUTO = 0,
+    CMAES_EIG_JACOBI = 1,
+    CMAES_EIG_TRIDIAGONAL = 2
+} cmaes_eig_method;
+
 typedef struct cmaes_options {
     int precision;        /* cmaes_precision                                  */
     int max_restarts;     /* descents after the first; K_max = 2^max_restarts */
@@ -107,6 +125,7 @@ typedef struct cmaes_options {
                           /* (Algorithm 2). 1: it pauses (cmaes_query reports   */
                           /* done = 2) until cmaes_restart resumes it, so the   */
                           /* host can schedule descents (K-Replicated, §3.2.2)  */
+    int eig_method;       /* cmaes_eig_method: eigensolver for 32 < n <= 4096   */
 } cmaes_options;
 
 /* Snapshot of one search (checkpoint / resume, and teacher-forced checks).
@@ -260,6 +279,16 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches,
 cmaes_status cmaes_eig_stats(cmaes_t h, int s, long long* decompositions,
                              long long* sweeps, long long* rotations,
                              long long* sweeps32);
+
+/* Device time of the stages of the tridiagonal eigensolver route, summed over
+ * the generations run with profiling enabled (cmaes_set_profiling): ms[0]
+ * Householder reduction, ms[1] eigenvalues (splitting, bisection, ranks),
+ * ms[2] eigenvectors of T by inverse iteration, ms[3] Gram-Schmidt inside
+ * clusters of close eigenvalues, ms[4] Newton-Schulz orthogonalisation,
+ * ms[5] back-transformation and canonical form. ms: host array of 6;
+ * reset != 0 zeroes the sums. Zero when
+ * no search takes that route. Synchronises with the handle's stream. */
+cmaes_status cmaes_eig_stage_times(cmaes_t h, double* ms, int reset);
 
 /* Number of kernel launches issued by the handle since creation. */
 long long cmaes_kernel_launches(cmaes_t h);

@@ -21,12 +21,14 @@ __all__ = [
     "cmaes_tell", "cmaes_step_batch", "cmaes_sync", "cmaes_restart", "cmaes_best",
     "cmaes_get_state", "cmaes_set_state", "cmaes_get_generation", "cmaes_query",
     "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
+    "cmaes_eig_stage_times",
     "cmaes_ask_async", "cmaes_tell_async",
     "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_inject_status", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
 
 FP64, MIXED_TF32, MIXED_BF16 = 0, 1, 2
+EIG_AUTO, EIG_JACOBI, EIG_TRIDIAGONAL = 0, 1, 2
 OBJ_ELLIPSOID, OBJ_RASTRIGIN, OBJ_SPHERE = 1, 2, 3
 PHASES = ("sample", "objective", "update", "cov", "eig", "stop")
 
@@ -48,7 +50,7 @@ class cmaes_options(ctypes.Structure):
                 ("f_target", ctypes.c_double), ("box_lo", ctypes.c_double),
                 ("box_hi", ctypes.c_double), ("tol_hist_fun", ctypes.c_double),
                 ("tol_x_factor", ctypes.c_double), ("cond_max", ctypes.c_double),
-                ("restart_hold", ctypes.c_int)]
+                ("restart_hold", ctypes.c_int), ("eig_method", ctypes.c_int)]
 
 
 _DP = ctypes.POINTER(ctypes.c_double)
@@ -104,6 +106,7 @@ def lib():
         "cmaes_phase_times": (I, [H, _DP, ctypes.POINTER(ctypes.c_longlong), I]),
         "cmaes_kernel_launches": (ctypes.c_longlong, [H]),
         "cmaes_eig_stats": (I, [H, I] + [ctypes.POINTER(ctypes.c_longlong)] * 4),
+        "cmaes_eig_stage_times": (I, [H, _DP, I]),
         "cmaes_evaluate_noalloc": (I, [I, I, I, V, I, V, I, V, V, V, V]),
         "cmaes_ask_async": (I, [H, I, I, ctypes.POINTER(V), ctypes.POINTER(ctypes.c_int), V]),
         "cmaes_tell_async": (I, [H, I, I, ctypes.POINTER(V), V]),
@@ -317,6 +320,18 @@ def cmaes_eig_stats(h, s):
     v = [ctypes.c_longlong() for _ in range(4)]
     _check(h, lib().cmaes_eig_stats(h, s, *[ctypes.byref(x) for x in v]))
     return dict(zip(("decompositions", "sweeps", "rotations", "sweeps32"), (x.value for x in v)))
+
+
+EIG_STAGES = ("reduction", "eigenvalues", "eigenvectors", "clusters", "orthogonalisation",
+              "backtransform")
+
+
+def cmaes_eig_stage_times(h, reset=False):
+    """Device ms of the tridiagonal route's stages over the profiled
+    generations (see include/cmaes.h)."""
+    ms = (ctypes.c_double * len(EIG_STAGES))()
+    _check(h, lib().cmaes_eig_stage_times(h, ms, 1 if reset else 0))
+    return dict(zip(EIG_STAGES, ms))
 
 
 def probe_fma_tflops(precision=64, blocks_per_sm=4, repeats=5):

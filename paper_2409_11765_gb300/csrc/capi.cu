@@ -16,6 +16,7 @@
 #include <cstdio>
 #include <cstring>
 #include <string>
+#include <utility>
 #include <vector>
 
 #include "../../include/cmaes.h"
@@ -51,6 +52,19 @@ struct cmaes_s {
   bool any_rotated = false, any_sphere = false;
   bool any_plain_eig = false;  // a search outside the refined eigensolver route (warm start B^T C B by k_eig_gemm_*)
   int max_n_big = 0;           // largest n of the searches whose FP32 Jacobi runs over many CTAs
+  // tridiagonal route: largest n, the CTA -> (search, member, group size) table
+  // of the cooperative reduction, and one barrier counter per search
+  int max_n_trd = 0;
+  int4* d_trd_grp = nullptr;
+  int trd_grp_blocks = 0;
+  std::vector<std::pair<int, int>> trd_chunks;  // (first CTA, CTAs) of each cooperative launch
+  // per-stage times of the tridiagonal route in profiling mode: one set of
+  // kTrdStages + 1 events per profiled generation, drained with the phases
+  std::vector<cudaEvent_t> trd_pool;
+  int trd_pending = 0;
+  double trd_stage_ms[kTrdStages] = {0};
+  cudaEvent_t* trd_marks = nullptr;  // events for the eigendecomposition being enqueued
+  unsigned* d_trd_bar = nullptr;
   std::vector<Search> hs_probe;  // host copy of the searches, read between FP32 Jacobi sweeps
   long long launches = 0;
   // profiling
@@ -290,6 +304,18 @@ static int enqueue_jacobi32_big(cmaes_t h, int s0, int s1, cudaStream_t st) {
 
 static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
   TileMap sq = h->tiles(TK_SQUARE, s0, s1);
+  if (h->max_n_trd > 0) {
+    // the cooperative reduction always covers every search of the handle (its
+    // group table is fixed at create); the searches outside [s0, s1) that
+    // are due are reduced too, which only repeats their decomposition
+    const int nl = launch_eig_trd(h->dS, h->d_trd_grp, h->trd_chunks.data(), static_cast<int>(h->trd_chunks.size()),
+                                  h->d_trd_bar, h->count, s0, s1, h->tiles(TK_TRD, s0, s1),
+                                  h->tiles(TK_TRDBIS, s0, s1), h->tiles(TK_TRDSYM, s0, s1),
+                                  h->tiles(TK_TRDSQ, s0, s1),
+                                  h->tiles(TK_TRDBT, s0, s1), h->max_n_trd, st, h->trd_marks);
+    h->launches += nl;
+    h->phase_launch[kPhaseEig] += nl;
+  }
   {
     TileMap tfl = h->tiles(TK_FLAT, s0, s1);
     TileMap tsy = h->tiles(TK_FLATSYM, s0, s1);
@@ -336,7 +362,23 @@ static cmaes_status record_event(cmaes_t h, int idx, cudaStream_t st) {
   return CMAES_OK;
 }
 
+static cmaes_status drain_trd_events(cmaes_t h) {
+  if (h->trd_pending == 0) return CMAES_OK;
+  const int need = kTrdStages + 1;
+  CUDA_TRY(h, cudaEventSynchronize(h->trd_pool[h->trd_pending * need - 1]));
+  for (int p = 0; p < h->trd_pending; ++p)
+    for (int k = 0; k < kTrdStages; ++k) {
+      float ms = 0.f;
+      CUDA_TRY(h, cudaEventElapsedTime(&ms, h->trd_pool[p * need + k], h->trd_pool[p * need + k + 1]));
+      h->trd_stage_ms[k] += ms;
+    }
+  h->trd_pending = 0;
+  return CMAES_OK;
+}
+
 static cmaes_status drain_events(cmaes_t h) {
+  cmaes_status rt = drain_trd_events(h);
+  if (rt != CMAES_OK) return rt;
   if (h->pending.empty()) return CMAES_OK;
   CUDA_TRY(h, cudaEventSynchronize(h->pool[h->pending.back().first + kNumPhases]));
   for (const PendingEvents& p : h->pending) {
@@ -410,6 +452,25 @@ static cmaes_status enqueue_generation(cmaes_t h, int s0, int s1, cudaStream_t s
     if (rg != CMAES_OK) return rg;
   }
   auto run = [&](int k) -> cmaes_status {
+    if (k == kPhaseEig && prof && h->max_n_trd > 0) {
+      // profiling: enqueued directly, with events between the stages of the
+      // tridiagonal route
+      const int need = kTrdStages + 1;
+      if (h->trd_pending >= 256) {
+        cmaes_status rd = drain_trd_events(h);
+        if (rd != CMAES_OK) return rd;
+      }
+      while (static_cast<int>(h->trd_pool.size()) < (h->trd_pending + 1) * need) {
+        cudaEvent_t e;
+        CUDA_TRY(h, cudaEventCreate(&e));
+        h->trd_pool.push_back(e);
+      }
+      h->trd_marks = h->trd_pool.data() + h->trd_pending * need;
+      enqueue_phase(h, k, s0, s1, st);
+      h->trd_marks = nullptr;
+      ++h->trd_pending;
+      return CMAES_OK;
+    }
     if (!graphed || (k == kPhaseEig && h->max_n_big > 0)) {
       enqueue_phase(h, k, s0, s1, st);
       return CMAES_OK;
@@ -496,6 +557,9 @@ void cmaes_destroy(cmaes_t h) {
   if (h->dS) cudaFree(h->dS);
   if (h->d_off) cudaFree(h->d_off);
   if (h->d_err) cudaFree(h->d_err);
+  if (h->d_trd_grp) cudaFree(h->d_trd_grp);
+  for (cudaEvent_t e : h->trd_pool) cudaEventDestroy(e);
+  if (h->d_trd_bar) cudaFree(h->d_trd_bar);
   if (h->stream) cudaStreamDestroy(h->stream);
   delete h;
 }
@@ -515,6 +579,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   if (opt.max_restarts < 0 || opt.max_restarts > 255)
     return set_error(nullptr, CMAES_EINVAL, "max_restarts must be in [0, 255]");
   if (!(opt.box_lo < opt.box_hi)) return set_error(nullptr, CMAES_EINVAL, "box_lo must be < box_hi");
+  if (opt.eig_method < CMAES_EIG_AUTO || opt.eig_method > CMAES_EIG_TRIDIAGONAL)
+    return set_error(nullptr, CMAES_EINVAL, "unknown eig_method %d", opt.eig_method);
 
   cmaes_t h = new cmaes_s();
   h->count = count;
@@ -565,6 +631,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     cov_split(n, x.mu_cap, &x.cov_kc, &x.cov_nch);
     x.mixed = h->mixed ? opt.precision : 0;
     x.kp = (n + 31) & ~31;
+    x.trd = (eig_refined_route(n) &&
+             (opt.eig_method == CMAES_EIG_TRIDIAGONAL || (opt.eig_method == CMAES_EIG_AUTO && n > kEigAutoTrdN)))
+                ? 1 : 0;
     if (h->mixed) tc_cov_split(n, x.mu_cap, &x.covm_kc, &x.covm_nch);
     const size_t ldn = x.ldn, n_ = n, lc = x.lam_cap, kp = x.kp;
     size_t b = 0;
@@ -585,12 +654,13 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += 4 * align256(ldn * lc * 8);                 // Z Y X U
     }
     b += 6 * align256(ldn * n_ * 8);                   // C B BD Q EA ET
-    if (eig_refined_route(n)) {
-      b += 3 * align256(ldn * n_ * 8);  // EX EG EH
+    if (eig_refined_route(n)) b += 3 * align256(ldn * n_ * 8);  // EX EG EH
+    if (eig_refined_route(n) && !x.trd) {
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * jlog_pairs(n) * 8);  // jlog
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * 4);                  // jlog_r
     }
-    if (eig_big_route(n)) {
+    if (x.trd) b += align256(ldn * kTrdVectors * 8) + align256(ldn * kTrdInts * 4);
+    if (eig_big_route(n) && !x.trd) {
       b += align256(jb_buf_floats(n) * 4);                         // jb_buf
       b += align256(static_cast<size_t>(jlog_pairs(n)) * 16);      // jb_rec
     }
@@ -600,10 +670,14 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     total += b;
     if (n > h->max_n) h->max_n = n;
     if (!eig_refined_route(n)) h->any_plain_eig = true;
-    if (eig_big_route(n) && n > h->max_n_big) h->max_n_big = n;
-    int* jm = n <= kJacobiSmallN ? &h->max_n_small_jacobi
-              : n <= kJacobiClusterN ? &h->max_n_cluster_jacobi : &h->max_n_global_jacobi;
-    if (n > *jm) *jm = n;
+    if (x.trd) {
+      if (n > h->max_n_trd) h->max_n_trd = n;
+    } else {
+      if (eig_big_route(n) && n > h->max_n_big) h->max_n_big = n;
+      int* jm = n <= kJacobiSmallN ? &h->max_n_small_jacobi
+                : n <= kJacobiClusterN ? &h->max_n_cluster_jacobi : &h->max_n_global_jacobi;
+      if (n > *jm) *jm = n;
+    }
   }
   h->arena_bytes = total;
   cudaError_t e = cudaMalloc(&h->arena, total);
@@ -670,10 +744,16 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       x.EX = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EG = reinterpret_cast<double*>(take(ldn * n_ * 8));
       x.EH = reinterpret_cast<double*>(take(ldn * n_ * 8));
+    }
+    if (eig_refined_route(x.n) && !x.trd) {
       x.jlog = reinterpret_cast<float*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * jlog_pairs(x.n) * 8));
       x.jlog_r = reinterpret_cast<int*>(take(static_cast<size_t>(jlog_steps_cap(x.n)) * 4));
     }
-    if (eig_big_route(x.n)) {
+    if (x.trd) {
+      x.trd_v = reinterpret_cast<double*>(take(ldn * kTrdVectors * 8));
+      x.trd_i = reinterpret_cast<int*>(take(ldn * kTrdInts * 4));
+    }
+    if (eig_big_route(x.n) && !x.trd) {
       x.jb_buf = reinterpret_cast<float*>(take(jb_buf_floats(x.n) * 4));
       x.jb_rec = reinterpret_cast<float*>(take(static_cast<size_t>(jlog_pairs(x.n)) * 16));
     }
@@ -693,6 +773,59 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   CREATE_TRY(cudaMalloc(&h->d_err, sizeof(int)));
   CREATE_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   for (int s = 0; s < count; ++s) h->hs[s].err = h->d_err;
+  if (h->max_n_trd > 0) {
+    CREATE_TRY(cudaMalloc(&h->d_trd_bar, sizeof(unsigned) * count));
+    CREATE_TRY(cudaMemsetAsync(h->d_trd_bar, 0, sizeof(unsigned) * count, h->stream));
+    for (int s = 0; s < count; ++s)
+      if (h->hs[s].trd) h->hs[s].trd_bar = h->d_trd_bar + s;
+    // groups of the cooperative reduction: every tridiagonal-route search gets
+    // CTAs in proportion to n^3 (at least one, at most n / 16), within what
+    // can be resident at once
+    int dev = 0, sms = 0;
+    CREATE_TRY(cudaGetDevice(&dev));
+    CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    trd_set_attributes(h->max_n_trd);
+    const int per_sm = trd_sytrd_blocks_per_sm(h->max_n_trd);
+    long long budget = static_cast<long long>(per_sm) * sms;
+    double wsum = 0.0;
+    int ntrd = 0;
+    for (int s = 0; s < count; ++s)
+      if (h->hs[s].trd) {
+        wsum += std::pow(static_cast<double>(h->hs[s].n), 3.0);
+        ++ntrd;
+      }
+    if (budget < 1) {
+      set_error(h, CMAES_EUNSUPPORTED, "the tridiagonal reduction cannot be resident on this device");
+      return fail(CMAES_EUNSUPPORTED);
+    }
+    // groups in search order, cut into launches of at most `budget` CTAs that
+    // never split a group (more searches than resident CTAs: one CTA each,
+    // several launches)
+    const long long spare = budget > ntrd ? budget - ntrd : 0;
+    std::vector<int4> grp;
+    h->trd_chunks.clear();
+    int chunk_start = 0;
+    for (int s = 0; s < count; ++s) {
+      const Search& x = h->hs[s];
+      if (!x.trd) continue;
+      const double share = std::pow(static_cast<double>(x.n), 3.0) / wsum;
+      int G = static_cast<int>(std::floor(share * static_cast<double>(spare))) + 1;
+      // at least 32 columns per CTA, and enough work per step to outweigh
+      // the group barrier (n^2 / 32768: one CTA below n = 181)
+      G = std::min(G, std::max(1, std::min(x.n / 32, static_cast<int>(static_cast<long long>(x.n) * x.n / 32768))));
+      if (static_cast<long long>(grp.size()) + G - chunk_start > budget) {
+        h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
+        chunk_start = static_cast<int>(grp.size());
+      }
+      for (int r = 0; r < G; ++r) grp.push_back(make_int4(s, r, G, 0));
+    }
+    h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
+    h->trd_grp_blocks = static_cast<int>(grp.size());
+    CREATE_TRY(cudaMalloc(&h->d_trd_grp, sizeof(int4) * grp.size()));
+    CREATE_TRY(cudaMemcpyAsync(h->d_trd_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice,
+                               h->stream));
+    CREATE_TRY(cudaStreamSynchronize(h->stream));  // grp (host vector) leaves scope
+  }
   CREATE_TRY(cudaMalloc(&h->dS, sizeof(Search) * count));
   CREATE_TRY(cudaMemcpyAsync(h->dS, h->hs.data(), sizeof(Search) * count, cudaMemcpyHostToDevice, h->stream));
   // tile prefix sums per kind
@@ -719,12 +852,17 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TCOBJ: t = h->mixed ? tiles_tc_objective(x.lam_cap) : 0; break;
         case TK_TCCOVP: t = h->mixed ? tiles_tc_sym(x.n) * x.covm_nch : 0; break;
         case TK_TCSYM: t = h->mixed ? 16 * tiles_tc_sym(x.n) : 0; break;  // reduce: 16 blocks per tile
-        case TK_FLAT: t = eig_refined_route(x.n) ? tiles_flat(x.n) : 0; break;
+        case TK_FLAT: t = eig_refined_route(x) ? tiles_flat(x.n) : 0; break;
         case TK_REEVAL: t = h->mixed ? tiles_reeval(x.n) : 0; break;
-        case TK_FLATSYM: t = eig_refined_route(x.n) ? tiles_flat_sym(x.n) : 0; break;
-        case TK_JBBLK: t = tiles_jb_blocks(x.n); break;
-        case TK_JBLOAD: t = tiles_jb_load(x.n); break;
-        case TK_JBROWS: t = tiles_jb_rows(x.n); break;
+        case TK_FLATSYM: t = eig_refined_route(x) ? tiles_flat_sym(x.n) : 0; break;
+        case TK_TRD: t = x.trd ? tiles_trd(x.n) : 0; break;
+        case TK_TRDBIS: t = x.trd ? tiles_trd_bis(x.n) : 0; break;
+        case TK_TRDSYM: t = x.trd ? tiles_trd_sym(x.n) : 0; break;
+        case TK_TRDSQ: t = x.trd ? tiles_trd_sq(x.n) : 0; break;
+        case TK_TRDBT: t = x.trd ? tiles_trd_bt(x.n) : 0; break;
+        case TK_JBBLK: t = x.trd ? 0 : tiles_jb_blocks(x.n); break;
+        case TK_JBLOAD: t = x.trd ? 0 : tiles_jb_load(x.n); break;
+        case TK_JBROWS: t = x.trd ? 0 : tiles_jb_rows(x.n); break;
       }
       o[s] = static_cast<int>(acc);
       acc += t;
@@ -1105,6 +1243,17 @@ cmaes_status cmaes_phase_times(cmaes_t h, double* ms, long long* launches, int r
       h->phase_ms[k] = 0.0;
       h->phase_launch[k] = 0;
     }
+  }
+  return CMAES_OK;
+}
+
+cmaes_status cmaes_eig_stage_times(cmaes_t h, double* ms, int reset) {
+  CHECK_HANDLE(h);
+  cmaes_status r = drain_events(h);
+  if (r != CMAES_OK) return r;
+  for (int k = 0; k < kTrdStages; ++k) {
+    if (ms) ms[k] = h->trd_stage_ms[k];
+    if (reset) h->trd_stage_ms[k] = 0.0;
   }
   return CMAES_OK;
 }

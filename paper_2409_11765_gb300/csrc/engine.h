@@ -5,7 +5,9 @@
 // panels are ldn x lam_cap column-major (one candidate per column), so a
 // column starts on a 128-byte boundary.
 #pragma once
+#include <cstddef>
 #include <cstdint>
+#include <utility>
 #include <cuda_runtime.h>
 
 namespace cmaes_gb300 {
@@ -83,6 +85,11 @@ struct Search {
   int jb_pend, jb_done;  // that check's pending flag and CTA count
   double jb_shift, jb_scale;
   int *err;           // device status word shared by the handle (kDevErr* bits)
+  // tridiagonal route of the eigendecomposition (kernels_eig_trd.cu)
+  int trd, trd_pad_;  // 1: this search's eigendecomposition takes the tridiagonal route
+  double* trd_v;      // 11 x ldn doubles: d, e, split e, e^2, tau, eigenvalues (two orders), p and p.v buffers, scalars
+  int* trd_i;         // 4 x ldn ints: block start / end, rank, cluster start
+  unsigned* trd_bar;  // the group barrier counter of the reduction
 };
 
 // Flattened tiles of one kernel over a contiguous range of searches:
@@ -111,7 +118,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_TRD, TK_TRDBIS, TK_TRDSYM, TK_TRDSQ, TK_TRDBT, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -146,7 +153,7 @@ constexpr int kJacobiClusterN = 256;
 constexpr int kEigMixedMaxN = 160;
 constexpr int kEigBigMaxN = 4096;
 __host__ __device__ inline bool eig_refined_route(int n) { return n > kJacobiSmallN && n <= kEigBigMaxN; }
-__host__ __device__ inline bool eig_refined_route(const Search& s) { return eig_refined_route(s.n); }
+__host__ __device__ inline bool eig_refined_route(const Search& s) { return !s.trd && eig_refined_route(s.n); }
 __host__ __device__ inline bool eig_big_route(int n) { return n > kEigMixedMaxN && n <= kEigBigMaxN; }
 // The FP32 Jacobi of that route runs at most kJ32MaxSweeps sweeps of N - 1
 // round-robin steps (N = n rounded up to even) in one CTA and logs the
@@ -204,5 +211,24 @@ void launch_jlog_big(Search* S, TileMap trows, int max_n, cudaStream_t st);
 
 // Error text of calls that have no handle (read by cmaes_last_error(NULL)).
 void set_global_error(const char* msg);
+
+// tridiagonal route (kernels_eig_trd.cu): 32 < n <= kEigBigMaxN; the default
+// above kEigAutoTrdN (below it the FP32 Jacobi of the refined route, in one
+// CTA's shared memory, is faster)
+constexpr int kEigAutoTrdN = kEigMixedMaxN;
+constexpr int kTrdVectors = 11;  // Search::trd_v, in ldn doubles
+constexpr int kTrdInts = 4;      // Search::trd_i, in ldn ints
+int tiles_trd(int n);      // 128 eigenvalues per tile
+int tiles_trd_bis(int n);  // 16 eigenvalues per tile (8 lanes each)
+int tiles_trd_sym(int n);  // upper 64 x 64 tiles of n x n
+int tiles_trd_sq(int n);   // all 64 x 64 tiles of n x n
+int tiles_trd_bt(int n);   // column groups of the back-transformation
+size_t trd_sytrd_smem(int max_n);
+int trd_sytrd_blocks_per_sm(int max_n);
+void trd_set_attributes(int max_n);
+constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
+int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
+                   int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
+                   TileMap tbt, int max_n, cudaStream_t st, cudaEvent_t* marks);
 
 }  // namespace cmaes_gb300

@@ -52,7 +52,9 @@ int jacobi_smem_max_n() {
 
 // Searches whose warm start is prepared by the refined route
 // (kernels_eig_mixed.cu) skip the FP64 B^T C B below.
-__device__ __forceinline__ bool mixed_route(const Search& s) { return eig_refined_route(s); }
+// searches whose decomposition another route computes (the refined
+// Jacobi route or the tridiagonal route) skip the plain warm start
+__device__ __forceinline__ bool mixed_route(const Search& s) { return eig_refined_route(s) || s.trd; }
 
 // ET = C B (square tiles; only searches whose decomposition is due).
 __global__ void __launch_bounds__(256) k_eig_gemm_CB(Search* S, TileMap tm) {
@@ -116,7 +118,7 @@ __global__ void __launch_bounds__(kJacobiNT) k_jacobi(Search* S, int s0, int lo_
   __shared__ long long sh_rot;
   __shared__ int sh_m;  // rotating pairs of the current step
   Search& s = S[s0 + blockIdx.x];
-  if (s.done || !s.eig_due) return;
+  if (s.done || !s.eig_due || s.trd) return;
   const int n = s.n, ldn = s.ldn;
   if (n <= lo_n || n > hi_n) return;
   const int N = n + (n & 1), P = N / 2;

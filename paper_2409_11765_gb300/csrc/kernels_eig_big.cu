@@ -40,7 +40,7 @@ constexpr float kJbTol = 1e-6f;  // as the single-CTA FP32 Jacobi
 constexpr float kJbTol2 = kJbTol * kJbTol;
 
 __device__ __forceinline__ bool big_due(const Search& s) {
-  return !s.done && s.eig_due && eig_big_route(s.n);
+  return !s.done && s.eig_due && !s.trd && eig_big_route(s.n);
 }
 
 __host__ __device__ inline long long jb_nb(int P) { return static_cast<long long>(P) * (P - 1) / 2; }

@@ -1,0 +1,873 @@
+// kernels_eig_trd.cu -- the tridiagonal route of the eigendecomposition
+// C = B D^2 B^T (32 < n <= kEigBigMaxN; the default route).
+//
+// The paper computes B and D with LAPACK's dsyev (§3.1), i.e. Householder
+// reduction to tridiagonal form followed by a tridiagonal eigensolver. On
+// GB300 FP64 issues at 1/64 of the FP32 rate, so the route is built for few
+// FP64 flops and few sequential steps, all in FP64 (no refinement needed):
+//   1. Householder tridiagonalisation T = Q^T C Q (unblocked, lower part;
+//      Golub & Van Loan §8.3.1), by a group of CTAs per search in one
+//      cooperative launch: per step every CTA of the group forms the reflector
+//      of column k itself (the same fixed-order arithmetic everywhere), then
+//      each CTA applies the pending rank-2 update A <- A - v w^T - w v^T of the
+//      previous step to the columns it owns while it accumulates the symmetric
+//      product p = tau A v for the new v: one pass over the trailing matrix and
+//      one group barrier per step.
+//   2. Splitting: off-diagonal entries below 4 sqrt(n) eps64 ||T|| are set to
+//      zero, which cuts T into independent blocks (this is where the repeated
+//      eigenvalues of a low-rank update of a multiple of I separate).
+//   3. Eigenvalues of each block by bisection on Sturm counts (one thread per
+//      eigenvalue), to an absolute accuracy of 4 eps64 ||T||.
+//   4. Eigenvectors of each block by inverse iteration (Gaussian elimination
+//      with partial pivoting on T - lambda I, three solves from a
+//      pseudo-random start); vectors of one block whose eigenvalues lie within
+//      1e-13 ||T|| of each other (where inverse iteration may return nearly
+//      parallel vectors) are orthogonalised by modified Gram-Schmidt (twice),
+//      in chunks of at most 64 consecutive vectors: a longer chain is a
+//      repeated eigenvalue spread by rounding, whose vectors come from
+//      independent pseudo-random starts and overlap little across chunks.
+//   5. Newton-Schulz steps V <- V + V (I - V^T V) / 2 restore orthogonality
+//      to rounding: inverse iteration leaves pairs with small absolute gaps
+//      (the small eigenvalues of an ill-conditioned C, the spread-out copies
+//      of a repeated eigenvalue) off by about eps64 ||T|| / gap, at most
+//      ~1e-3 outside the Gram-Schmidt clusters. V^T V is formed in FP64, the
+//      correction (of the size of that defect) in FP32; up to three steps,
+//      each after the first only when the previous one started from a defect
+//      above 5e-9.
+//   6. Back-transformation B = Q V with the stored reflectors, then the
+//      canonical form shared with the Jacobi route: columns in ascending
+//      eigenvalue order, each column's entry of largest magnitude positive,
+//      the PD guard on the eigenvalues.
+// Every reduction has a fixed order, so a search gives the same bits alone
+// and inside any batch.
+#include <algorithm>
+#include <cfloat>
+#include <cmath>
+#include "device_common.cuh"
+
+namespace cmaes_gb300 {
+
+// --------------------------------------------------------------------------
+// Scratch of one search (Search::trd_v: TV_COUNT vectors of ldn doubles,
+// Search::trd_i: TI_COUNT vectors of ldn ints) and its matrices: W (the matrix
+// being reduced) = EA, reflectors = EX (column k holds v_k in rows k+1..),
+// eigenvectors of T = ET (column t), inverse-iteration factors = EA, EG, EH
+// (after the reduction), I - V^T V in FP32 = EG, the Newton-Schulz iterates
+// alternate between ET and EA and end in EA.
+// --------------------------------------------------------------------------
+enum { TV_D = 0, TV_E, TV_ES, TV_E2, TV_TAU, TV_LAMB, TV_LAMS, TV_P0, TV_P1, TV_SD, TV_SCAL };
+enum { TI_B0 = 0, TI_B1, TI_RANK, TI_CL0 };
+// scalars at TV_SCAL: ||T|| bound, pivmin, split threshold, cluster threshold,
+// and the orthogonality defect max |(I - V^T V) / 2| before each Newton-Schulz
+// step (as ordered bit patterns for atomicMax)
+constexpr double kTrdSplit = 4.0;
+constexpr double kTrdClus = 1e-13;
+constexpr int kTrdClusMax = 64;      // Gram-Schmidt chunk of a longer cluster
+constexpr int kTrdNsSteps = 3;
+constexpr double kTrdNsSkip = 5e-9;  // one step leaves 1.5 (2 * 5e-9)^2 < eps64
+constexpr double kTrdEps = 0x1p-53;
+constexpr long long kTrdWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
+constexpr int kTrdNT = 256;
+
+__device__ __forceinline__ bool trd_due(const Search& s) { return s.trd && !s.done && s.eig_due; }
+
+__device__ __forceinline__ double* tv(const Search& s, int which) {
+  return s.trd_v + static_cast<long long>(which) * s.ldn;
+}
+__device__ __forceinline__ int* ti(const Search& s, int which) {
+  return s.trd_i + static_cast<long long>(which) * s.ldn;
+}
+
+__device__ __forceinline__ double warp_sum_xor(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__device__ __forceinline__ unsigned ld_acquire_u32(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+// Barrier of the G CTAs of one search. The launch is cooperative, so every
+// CTA of the group is resident; the wait is still bounded: after ~1 s the
+// device status word records a time-out and the CTA leaves the reduction.
+__device__ bool trd_group_sync(unsigned* ctr, unsigned target, int* err, int* sh_ok) {
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    __threadfence();
+    atomicAdd(ctr, 1u);
+    const long long t0 = clock64();
+    int ok = 1;
+    while (ld_acquire_u32(ctr) < target) {
+      if (clock64() - t0 > kTrdWaitCycles) {
+        atomicOr(err, kDevErrTimeout);
+        ok = 0;
+        break;
+      }
+    }
+    __threadfence();
+    *sh_ok = ok;
+  }
+  __syncthreads();
+  return *sh_ok != 0;
+}
+
+// --------------------------------------------------------------------------
+// 1. Householder tridiagonalisation. CTA blockIdx.x works for search
+// grp[b].x as member grp[b].y of a group of grp[b].z CTAs; column j of the
+// trailing matrix belongs to member j mod G, and within it to warp
+// (j div G) mod 8. Dynamic shared memory: v and w of the previous step and v
+// of the current one (3 n doubles).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrdNT) k_trd_sytrd(Search* S, const int4* grp) {
+  extern __shared__ double tsm[];
+  __shared__ double red[kTrdNT / 32 + 8];
+  __shared__ int sh_ok;
+  const int4 g = grp[blockIdx.x];
+  Search& s = S[g.x];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const long long L = s.ldn;
+  const int r = g.y, G = g.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kTrdNT / 32;
+  double* W = s.EA;
+  double* Hv = s.EX;
+  const double* C = s.C;
+  double* d = tv(s, TV_D);
+  double* e = tv(s, TV_E);
+  double* tau = tv(s, TV_TAU);
+  double* pbuf = tv(s, TV_P0);  // two buffers: step k uses pbuf + (k & 1) L
+  double* sdot = tv(s, TV_SD);  // per-CTA partial p.v, two buffers of L / 2
+  unsigned* bar = s.trd_bar;
+  double* vprev = tsm;
+  double* wprev = tsm + n;
+  double* vcur = tsm + 2 * n;
+  // W = (C + C^T) / 2, owned columns only
+  for (int j = r; j < n; j += G)
+    for (int i = tid; i < n; i += kTrdNT) W[i + L * j] = 0.5 * (C[i + L * j] + C[j + L * i]);
+  for (int i = tid; i < n; i += kTrdNT) {
+    vprev[i] = 0.0;
+    wprev[i] = 0.0;
+  }
+  unsigned nb = 0;
+  if (G > 1) {
+    if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
+  } else {
+    __syncthreads();
+  }
+  for (int k = 0; k + 1 < n; ++k) {
+    // column k with the pending update of step k - 1
+    for (int i = k + tid; i < n; i += kTrdNT)
+      vcur[i] = fma(-wprev[i], vprev[k], fma(-vprev[i], wprev[k], __ldcg(&W[i + L * k])));
+    __syncthreads();
+    // its reflector (warp 0, fixed-order sum)
+    if (warp == 0) {
+      double part = 0.0;
+      for (int i = k + 2 + lane; i < n; i += 32) part = fma(vcur[i], vcur[i], part);
+      const double xn2 = warp_sum_xor(part);
+      if (lane == 0) {
+        const double alpha = vcur[k + 1];
+        double t = 0.0, beta = alpha, scale = 0.0;
+        if (xn2 > 0.0) {
+          beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        red[NW] = t;
+        red[NW + 1] = beta;
+        red[NW + 2] = scale;
+        red[NW + 3] = vcur[k];
+      }
+    }
+    __syncthreads();
+    const double t = red[NW], scale = red[NW + 2];
+    for (int i = k + 2 + tid; i < n; i += kTrdNT) vcur[i] *= scale;
+    if (tid == 0) vcur[k + 1] = 1.0;
+    __syncthreads();
+    if (r == 0) {
+      for (int i = k + 1 + tid; i < n; i += kTrdNT) Hv[i + L * k] = vcur[i];
+      if (tid == 0) {
+        d[k] = red[NW + 3];
+        e[k] = red[NW + 1];
+        tau[k] = t;
+      }
+    }
+    // owned columns j >= k + 1, two per warp at a time: pending update, then
+    // p_j = tau (A v)_j, and this CTA's share of p . v
+    double* pk = pbuf + (k & 1) * L;
+    const int m0 = (k + 1 > r) ? (k + 1 - r + G - 1) / G : 0;
+    double pv = 0.0;
+    for (int m = m0 + warp;; m += 2 * NW) {
+      const int j1 = r + G * m, j2 = r + G * (m + NW);
+      if (j1 >= n) break;
+      const bool two = j2 < n;
+      const int j2c = two ? j2 : j1;
+      const double vp1 = vprev[j1], wp1 = wprev[j1], vp2 = vprev[j2c], wp2 = wprev[j2c];
+      double q1 = 0.0, q2 = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) {
+        const double vi = vprev[i], wi = wprev[i], ci = vcur[i];
+        const double a1 = fma(-wi, vp1, fma(-vi, wp1, W[i + L * j1]));
+        W[i + L * j1] = a1;
+        q1 = fma(a1, ci, q1);
+        if (two) {
+          const double a2 = fma(-wi, vp2, fma(-vi, wp2, W[i + L * j2]));
+          W[i + L * j2] = a2;
+          q2 = fma(a2, ci, q2);
+        }
+        if (k == n - 2) d[n - 1] = a1;  // the last diagonal entry (i = j = n - 1)
+      }
+      q1 = t * warp_sum_xor(q1);
+      q2 = t * warp_sum_xor(q2);
+      if (lane == 0) {
+        pk[j1] = q1;
+        pv = fma(q1, vcur[j1], pv);
+        if (two) {
+          pk[j2] = q2;
+          pv = fma(q2, vcur[j2], pv);
+        }
+      }
+    }
+    if (lane == 0) red[warp] = pv;
+    __syncthreads();
+    double* sdk = sdot + (k & 1) * (L / 2);
+    if (tid == 0) {
+      double sp = 0.0;
+      for (int w = 0; w < NW; ++w) sp += red[w];
+      sdk[r] = sp;
+    }
+    if (G > 1) {
+      if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
+    } else {
+      __syncthreads();
+    }
+    // w = p - (tau / 2) (p . v) v, kept with v for the next step's update
+    if (warp == 0) {
+      double sp = 0.0;
+      for (int c = lane; c < G; c += 32) sp += __ldcg(&sdk[c]);
+      sp = warp_sum_xor(sp);
+      if (lane == 0) red[NW + 4] = 0.5 * t * sp;
+    }
+    for (int i = k + 1 + tid; i < n; i += kTrdNT) wprev[i] = __ldcg(&pk[i]);
+    __syncthreads();
+    const double half = red[NW + 4];
+    for (int i = k + 1 + tid; i < n; i += kTrdNT) {
+      wprev[i] = fma(-half, vcur[i], wprev[i]);
+      vprev[i] = vcur[i];
+    }
+    __syncthreads();
+  }
+}
+
+// --------------------------------------------------------------------------
+// Scans of one CTA over n entries (n <= 4096): last index u <= t with
+// flag(u) (prefix) or first index u >= t with flag(u) (suffix).
+// --------------------------------------------------------------------------
+template <int NT, class F>
+__device__ void scan_last_start(int n, const F& flag, int* out, int* sh) {
+  const int chunk = ceil_div(n, NT), c0 = threadIdx.x * chunk;
+  int last = -1;
+  for (int u = c0; u < c0 + chunk && u < n; ++u)
+    if (flag(u)) last = u;
+  sh[threadIdx.x] = last;
+  __syncthreads();
+  int carry = -1;
+  for (int q = 0; q < static_cast<int>(threadIdx.x); ++q) carry = max(carry, sh[q]);
+  for (int u = c0; u < c0 + chunk && u < n; ++u) {
+    if (flag(u)) carry = u;
+    out[u] = carry;
+  }
+  __syncthreads();
+}
+
+template <int NT, class F>
+__device__ void scan_first_end(int n, const F& flag, int* out, int* sh) {
+  const int chunk = ceil_div(n, NT), c0 = threadIdx.x * chunk;
+  int first = 0x7fffffff;
+  for (int u = min(c0 + chunk, n) - 1; u >= c0; --u)
+    if (flag(u)) first = u;
+  sh[threadIdx.x] = first;
+  __syncthreads();
+  int carry = 0x7fffffff;
+  for (int q = NT - 1; q > static_cast<int>(threadIdx.x); --q) carry = min(carry, sh[q]);
+  for (int u = min(c0 + chunk, n) - 1; u >= c0; --u) {
+    if (flag(u)) carry = u;
+    out[u] = carry + 1;  // block end (exclusive)
+  }
+  __syncthreads();
+}
+
+// --------------------------------------------------------------------------
+// 2. ||T|| bound, splitting and the blocks of T (one CTA per search).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrdNT) k_trd_blocks(Search* S, int s0) {
+  __shared__ double red[32];
+  __shared__ int shi[kTrdNT];
+  Search& s = S[s0 + blockIdx.x];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const double* d = tv(s, TV_D);
+  const double* e = tv(s, TV_E);
+  double* es = tv(s, TV_ES);
+  double* e2 = tv(s, TV_E2);
+  double* sc = tv(s, TV_SCAL);
+  double tn = 0.0, em = 0.0;
+  for (int i = threadIdx.x; i < n; i += kTrdNT) {
+    const double lo = i > 0 ? fabs(e[i - 1]) : 0.0, hi = i + 1 < n ? fabs(e[i]) : 0.0;
+    tn = fmax(tn, fabs(d[i]) + lo + hi);
+    em = fmax(em, hi);
+  }
+  tn = block_max<kTrdNT>(tn, red);
+  em = block_max<kTrdNT>(em, red);
+  const double split = kTrdSplit * sqrt(static_cast<double>(n)) * kTrdEps * tn;
+  for (int i = threadIdx.x; i + 1 < n; i += kTrdNT) {
+    const double x = fabs(e[i]) <= split ? 0.0 : e[i];
+    es[i] = x;
+    e2[i] = x * x;
+  }
+  if (threadIdx.x == 0) {
+    sc[0] = tn;
+    sc[1] = DBL_MIN * fmax(1.0, em * em);
+    sc[2] = split;
+    sc[3] = kTrdClus * tn;
+    sc[4] = 0.0;  // orthogonality defects before the Newton-Schulz steps
+    sc[5] = 0.0;
+    sc[6] = 0.0;
+  }
+  __syncthreads();
+  int* b0 = ti(s, TI_B0);
+  int* b1 = ti(s, TI_B1);
+  scan_last_start<kTrdNT>(n, [&](int u) { return u == 0 || es[u - 1] == 0.0; }, b0, shi);
+  scan_first_end<kTrdNT>(n, [&](int u) { return u == n - 1 || es[u] == 0.0; }, b1, shi);
+}
+
+// --------------------------------------------------------------------------
+// 3. Multisection: a group of 8 lanes finds eigenvalue t - b0 (ascending) of
+// its block; each round the 8 lanes take the Sturm counts at 8 interior points
+// of the bracket, which shrinks it 9-fold. The counts' reciprocals come from
+// an FP32 estimate and two Newton steps in FP64 (exact to rounding) instead of
+// an FP64 divide.
+// --------------------------------------------------------------------------
+constexpr int kTrdTT = 128;   // threads per tile of the per-eigenvalue kernels
+constexpr int kTrdBisLanes = 8;
+int tiles_trd(int n) { return ceil_div(n, kTrdTT); }
+int tiles_trd_bis(int n) { return ceil_div(n * kTrdBisLanes, kTrdTT); }
+
+__device__ __forceinline__ double fast_rcp(double q) {
+  const double aq = fabs(q);
+  if (aq > 1e-30 && aq < 1e30) {
+    double r = static_cast<double>(__frcp_rn(static_cast<float>(q)));
+    r = r * fma(-q, r, 2.0);
+    return r * fma(-q, r, 2.0);
+  }
+  return 1.0 / q;
+}
+
+__global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const int q = threadIdx.x % kTrdBisLanes;
+  const int t = tile * (kTrdTT / kTrdBisLanes) + threadIdx.x / kTrdBisLanes;
+  if (t >= n) return;  // uniform across the 8 lanes of a group
+  const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~(kTrdBisLanes - 1));
+  const double* d = tv(s, TV_D);
+  const double* es = tv(s, TV_ES);
+  const double* e2 = tv(s, TV_E2);
+  const double* sc = tv(s, TV_SCAL);
+  double* lamb = tv(s, TV_LAMB);
+  const int b0 = ti(s, TI_B0)[t], b1 = ti(s, TI_B1)[t];
+  if (b1 - b0 == 1) {
+    if (q == 0) lamb[t] = d[t];
+    return;
+  }
+  const double tn = sc[0], pivmin = sc[1];
+  double gl = INFINITY, gu = -INFINITY;
+  for (int j = b0; j < b1; ++j) {
+    const double rad = (j > b0 ? fabs(es[j - 1]) : 0.0) + (j + 1 < b1 ? fabs(es[j]) : 0.0);
+    gl = fmin(gl, d[j] - rad);
+    gu = fmax(gu, d[j] + rad);
+  }
+  const double atol = 4.0 * kTrdEps * tn;
+  const double fudge = 2.0 * kTrdEps * tn * (b1 - b0) + 2.0 * pivmin;
+  double lo = gl - fudge, hi = gu + fudge;
+  const int idx = t - b0;
+  for (int it = 0; it < 48 && hi - lo > atol; ++it) {
+    const double w = (hi - lo) / (kTrdBisLanes + 1);
+    const double x = lo + w * (q + 1);
+    int cnt = 0;
+    double qq = d[b0] - x;
+    if (fabs(qq) <= pivmin) qq = -pivmin;
+    cnt += qq < 0.0;
+    for (int j = b0 + 1; j < b1; ++j) {
+      qq = (d[j] - x) - e2[j - 1] * fast_rcp(qq);
+      if (fabs(qq) <= pivmin) qq = -pivmin;
+      cnt += qq < 0.0;
+    }
+    // points with count <= idx lie left of the eigenvalue: the bracket
+    // becomes [x_qlo, x_qlo+1] for the rightmost such point qlo
+    const unsigned le = __ballot_sync(gmask, cnt <= idx) & gmask;
+    const int base = (threadIdx.x & 31) & ~(kTrdBisLanes - 1);
+    const int qlo = le ? (31 - __clz(le)) - base : -1;
+    const double nlo = qlo >= 0 ? lo + w * (qlo + 1) : lo;
+    const double nhi = qlo + 1 < kTrdBisLanes ? lo + w * (qlo + 2) : hi;
+    if (!(nlo < nhi) || (nlo == lo && nhi == hi)) break;
+    lo = nlo;
+    hi = nhi;
+  }
+  if (q == 0) lamb[t] = 0.5 * (lo + hi);
+}
+
+// --------------------------------------------------------------------------
+// 4a. Ranks of the eigenvalues (ascending, ties by block-major index) and the
+// clusters of close eigenvalues within a block (one CTA per search).
+// --------------------------------------------------------------------------
+constexpr int kTrdSortNT = 1024;
+
+__device__ __forceinline__ long long order_key(double x) {
+  const long long b = __double_as_longlong(x);
+  return b >= 0 ? b : (b ^ 0x7fffffffffffffffLL);
+}
+
+__global__ void __launch_bounds__(kTrdSortNT) k_trd_rank(Search* S, int s0) {
+  __shared__ int shi[kTrdSortNT];
+  Search& s = S[s0 + blockIdx.x];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const double* lamb = tv(s, TV_LAMB);
+  double* lams = tv(s, TV_LAMS);
+  int* rank = ti(s, TI_RANK);
+  const int* b0 = ti(s, TI_B0);
+  const double ctol = tv(s, TV_SCAL)[3];
+  for (int t = threadIdx.x; t < n; t += kTrdSortNT) {
+    const long long kt = order_key(lamb[t]);
+    int r = 0;
+    for (int u = 0; u < n; ++u) {
+      const long long ku = order_key(lamb[u]);
+      r += (ku < kt) || (ku == kt && u < t);
+    }
+    rank[t] = r;
+    lams[r] = lamb[t];
+  }
+  scan_last_start<kTrdSortNT>(
+      n, [&](int u) { return u == b0[u] || !(lamb[u] - lamb[u - 1] <= ctol); }, ti(s, TI_CL0), shi);
+}
+
+// --------------------------------------------------------------------------
+// 4b. Inverse iteration (thread t, eigenvalue lamb[t] of its block): three
+// solves of (T - lambda I) x = x_prev by Gaussian elimination with partial
+// pivoting; the U factor's three diagonals go to scratch interleaved by
+// thread, the iterate lives in column t of ET.
+// --------------------------------------------------------------------------
+__device__ __forceinline__ double start_value(int t, int j) {
+  uint32_t h = static_cast<uint32_t>(t) * 0x9E3779B1u ^ (static_cast<uint32_t>(j) * 0x85EBCA77u);
+  h ^= h >> 15;
+  h *= 0x2C1B3C6Du;
+  h ^= h >> 12;
+  h *= 0x297A2D39u;
+  h ^= h >> 15;
+  return (static_cast<double>(h) + 0.5) * 0x1p-31 - 1.0;  // in (-1, 1)
+}
+
+__global__ void __launch_bounds__(kTrdTT) k_trd_invit(Search* S, TileMap tm) {
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n, t = tile * kTrdTT + threadIdx.x;
+  if (t >= n) return;
+  const long long L = s.ldn, nn = n;
+  const double* d = tv(s, TV_D);
+  const double* es = tv(s, TV_ES);
+  const double lam = tv(s, TV_LAMB)[t];
+  const double tiny = kTrdEps * tv(s, TV_SCAL)[0];
+  const int b0 = ti(s, TI_B0)[t], b1 = ti(s, TI_B1)[t];
+  double* x = s.ET + L * t;
+  for (int i = 0; i < n; ++i) x[i] = 0.0;
+  if (b1 - b0 == 1) {
+    x[t] = 1.0;
+    return;
+  }
+  double* u0 = s.EA;
+  double* u1 = s.EG;
+  double* u2 = s.EH;
+  auto piv_of = [&](double a) { return fabs(a) > tiny ? a : (a < 0.0 ? -tiny : tiny); };
+  for (int j = b0; j < b1; ++j) x[j] = start_value(t, j);
+  for (int it = 0; it < 3; ++it) {
+    double a = d[b0] - lam, b = es[b0], c = 0.0;
+    double y = x[b0];
+    for (int j = b0; j + 1 < b1; ++j) {
+      const double sub = es[j], nd = d[j + 1] - lam, nsup = (j + 2 < b1) ? es[j + 1] : 0.0;
+      const double yn = x[j + 1];
+      const long long o = j * nn + t;
+      if (fabs(a) >= fabs(sub)) {
+        const double piv = piv_of(a);
+        const double l = sub / piv;
+        u0[o] = piv;
+        u1[o] = b;
+        u2[o] = c;
+        x[j] = y;
+        y = yn - l * y;
+        a = nd - l * b;
+        b = nsup - l * c;
+      } else {
+        const double l = a / sub;
+        u0[o] = sub;
+        u1[o] = nd;
+        u2[o] = nsup;
+        x[j] = yn;
+        y = y - l * yn;
+        const double a2 = b - l * nd;
+        b = c - l * nsup;
+        a = a2;
+      }
+      c = 0.0;
+    }
+    // back substitution, then normalise
+    double xn1 = y / piv_of(a), xn2 = 0.0;
+    x[b1 - 1] = xn1;
+    double ss = xn1 * xn1;
+    for (int j = b1 - 2; j >= b0; --j) {
+      const long long o = j * nn + t;
+      const double v = (x[j] - u1[o] * xn1 - u2[o] * xn2) / u0[o];
+      x[j] = v;
+      xn2 = xn1;
+      xn1 = v;
+      ss = fma(v, v, ss);
+    }
+    const double inv = 1.0 / sqrt(ss);
+    for (int j = b0; j < b1; ++j) x[j] *= inv;
+  }
+}
+
+// --------------------------------------------------------------------------
+// 4c. Modified Gram-Schmidt (twice) inside each cluster of close eigenvalues
+// of one block; one warp per cluster, one CTA per search.
+// --------------------------------------------------------------------------
+// Modified Gram-Schmidt, twice, on vectors [c, ce) of rows [r0, r1) (one warp).
+__device__ void cluster_mgs(double* V, long long L, int c, int ce, int r0, int r1, int lane) {
+  double* vc = V + L * c;
+  {
+    double q = 0.0;
+    for (int i = r0 + lane; i < r1; i += 32) q = fma(vc[i], vc[i], q);
+    const double inv = 1.0 / sqrt(warp_sum_xor(q));
+    for (int i = r0 + lane; i < r1; i += 32) vc[i] *= inv;
+    __syncwarp();
+  }
+  for (int a = c + 1; a < ce; ++a) {
+    double* va = V + L * a;
+    for (int rep = 0; rep < 2; ++rep)
+      for (int b = c; b < a; ++b) {
+        const double* vb = V + L * b;
+        double p = 0.0;
+        for (int i = r0 + lane; i < r1; i += 32) p = fma(vb[i], va[i], p);
+        p = warp_sum_xor(p);
+        for (int i = r0 + lane; i < r1; i += 32) va[i] = fma(-p, vb[i], va[i]);
+        __syncwarp();
+      }
+    double q = 0.0;
+    for (int i = r0 + lane; i < r1; i += 32) q = fma(va[i], va[i], q);
+    const double inv = 1.0 / sqrt(warp_sum_xor(q));
+    for (int i = r0 + lane; i < r1; i += 32) va[i] *= inv;
+    __syncwarp();
+  }
+}
+
+__global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
+  Search& s = S[s0 + blockIdx.x];
+  if (!trd_due(s)) return;
+  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long L = s.ldn;
+  const int* cl0 = ti(s, TI_CL0);
+  const int* b0a = ti(s, TI_B0);
+  const int* b1a = ti(s, TI_B1);
+  double* V = s.ET;
+  int found = 0;
+  for (int c = 0; c < n; ++c) {
+    if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;  // clusters of two or more
+    if ((found++ % (kTrdNT / 32)) != warp) continue;
+    int ce = c + 1;
+    while (ce < n && cl0[ce] == c) ++ce;
+    for (int cc = c; cc < ce; cc += kTrdClusMax)
+      cluster_mgs(V, L, cc, min(ce, cc + kTrdClusMax), b0a[c], b1a[c], lane);
+  }
+}
+
+// --------------------------------------------------------------------------
+// 5. Newton-Schulz: M = (I - V^T V) / 2 in FP32 from an FP64 product (upper
+// 64 x 64 tiles, mirrored), then V' = V + V M with FP32 products (all tiles).
+// --------------------------------------------------------------------------
+int tiles_trd_sym(int n) { const int T = ceil_div(n, kGBM); return T * (T + 1) / 2; }
+int tiles_trd_sq(int n) { const int T = ceil_div(n, kGBM); return T * T; }
+
+__global__ void __launch_bounds__(kGNT) k_trd_gram(Search* S, TileMap tm, int pass) {
+  __shared__ GemmSmem sm;
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  double* sc = tv(s, TV_SCAL);
+  if (pass > 0 && __ldcg(&sc[3 + pass]) <= kTrdNsSkip) return;  // the previous step was enough
+  const int n = s.n, T = ceil_div(n, kGBM);
+  int bi = 0, rem = tile;  // upper tiles, row-block major: (bi, bj) with bj >= bi
+  while (rem >= T - bi) {
+    rem -= T - bi;
+    ++bi;
+  }
+  const int bj = bi + rem;
+  const long long L = s.ldn;
+  const double* V = (pass & 1) ? s.EA : s.ET;
+  float* M = reinterpret_cast<float*>(s.EG);
+  double dmax = 0.0;
+  gemm_tile_f64<false, true>(
+      n, n, n, bi * kGBM, bj * kGBN, [=] __device__(int i, int k) { return V[k + L * i]; },
+      [=] __device__(int k, int j) { return V[k + L * j]; },
+      [&] __device__(int i, int j, double g) {
+        const double m = 0.5 * ((i == j ? 1.0 : 0.0) - g);
+        M[i + L * j] = static_cast<float>(m);
+        M[j + L * i] = static_cast<float>(m);
+        dmax = fmax(dmax, fabs(m));
+      },
+      sm);
+  // the defect of this pass (non-negative doubles order like their bit patterns)
+  for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
+  if ((threadIdx.x & 31) == 0 && dmax > 0.0)
+    atomicMax(reinterpret_cast<unsigned long long*>(&sc[4 + pass]),
+              static_cast<unsigned long long>(__double_as_longlong(dmax)));
+}
+
+struct GemmSmem32 {
+  float As[kGBK][kGBM];
+  float Bs[kGBK][kGBN];
+};
+
+// Step `pass` (0, 1, 2) maps ET -> EA, EA -> ET, ET -> EA: V' = V + V M, or a
+// copy when the previous step started from a defect small enough (then no M
+// was formed); the result is in EA after the three.
+__global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass) {
+  __shared__ GemmSmem32 sm;
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n, T = ceil_div(n, kGBM);
+  const int i0 = (tile % T) * kGBM, j0 = (tile / T) * kGBN;
+  const long long L = s.ldn;
+  const double* V = (pass & 1) ? s.EA : s.ET;
+  double* Vo = (pass & 1) ? s.ET : s.EA;
+  const int tid = threadIdx.x, tr = tid & 15, tc = tid >> 4;
+  if (pass > 0 && __ldcg(&tv(s, TV_SCAL)[3 + pass]) <= kTrdNsSkip) {
+    for (int e = tid; e < kGBM * kGBN; e += kGNT) {
+      const int i = i0 + (e & (kGBM - 1)), j = j0 + e / kGBM;
+      if (i < n && j < n) Vo[i + L * j] = V[i + L * j];
+    }
+    return;
+  }
+  const float* M = reinterpret_cast<const float*>(s.EG);
+  float acc[4][4] = {};
+  for (int k0 = 0; k0 < n; k0 += kGBK) {
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      const int e = tid + q * kGNT;
+      const int ii = e & (kGBM - 1), kk = e >> 6;
+      const int gi = i0 + ii, gk = k0 + kk;
+      sm.As[kk][ii] = (gi < n && gk < n) ? static_cast<float>(V[gi + L * gk]) : 0.f;
+      const int kk2 = e & (kGBK - 1), jj = e >> 4;
+      const int gk2 = k0 + kk2, gj = j0 + jj;
+      sm.Bs[kk2][jj] = (gk2 < n && gj < n) ? M[gk2 + L * gj] : 0.f;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < kGBK; ++kk) {
+      float a[4], b[4];
+#pragma unroll
+      for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][tr + 16 * r];
+#pragma unroll
+      for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][tc + 16 * c];
+#pragma unroll
+      for (int r = 0; r < 4; ++r)
+#pragma unroll
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int r = 0; r < 4; ++r)
+#pragma unroll
+    for (int c = 0; c < 4; ++c) {
+      const int i = i0 + tr + 16 * r, j = j0 + tc + 16 * c;
+      if (i < n && j < n) Vo[i + L * j] = V[i + L * j] + static_cast<double>(acc[r][c]);
+    }
+}
+
+// --------------------------------------------------------------------------
+// 6. Back-transformation B = Q V' (reflectors applied in reverse order to R
+// columns held in shared memory, one warp per column), canonical sign, and
+// the column order of ascending eigenvalues.
+// --------------------------------------------------------------------------
+__host__ __device__ inline int trd_bt_cols(int n) { return n <= 3200 ? 8 : 6; }
+int tiles_trd_bt(int n) { return ceil_div(n, trd_bt_cols(n)); }
+size_t trd_bt_smem(int max_n) {
+  int best = 0;
+  for (int n = 1; n <= max_n; n += (n < 3200 ? 3199 : 1)) best = std::max(best, trd_bt_cols(n) * n);
+  best = std::max(best, trd_bt_cols(max_n) * max_n);
+  return static_cast<size_t>(best) * 8;
+}
+
+__global__ void __launch_bounds__(kTrdNT) k_trd_backtf(Search* S, TileMap tm) {
+  extern __shared__ double cols[];
+  int tile;
+  const int si = find_search(tm, tile);
+  Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n, R = trd_bt_cols(n);
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const long long L = s.ldn;
+  const int t0 = tile * R;
+  const int nc = min(R, n - t0);
+  const double* Vs = s.EA;
+  for (int c = 0; c < nc; ++c)
+    for (int i = threadIdx.x; i < n; i += kTrdNT) cols[c * n + i] = Vs[i + L * (t0 + c)];
+  __syncthreads();
+  if (warp < nc) {
+    double* x = cols + warp * n;
+    const double* tau = tv(s, TV_TAU);
+    const double* Hv = s.EX;
+    for (int k = n - 2; k >= 0; --k) {
+      const double tk = tau[k];
+      if (tk == 0.0) continue;
+      const double* v = Hv + L * k;
+      double p = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) p = fma(v[i], x[i], p);
+      p = tk * warp_sum_xor(p);
+      for (int i = k + 1 + lane; i < n; i += 32) x[i] = fma(-p, v[i], x[i]);
+      __syncwarp();
+    }
+    // sign: the entry of largest magnitude (the first on ties) positive
+    double best = -1.0, val = 0.0;
+    int bi = 0x7fffffff;
+    for (int i = lane; i < n; i += 32) {
+      const double a = fabs(x[i]);
+      if (a > best) {
+        best = a;
+        val = x[i];
+        bi = i;
+      }
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+      const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+      if (ob > best || (ob == best && oi < bi)) {
+        best = ob;
+        val = ov;
+        bi = oi;
+      }
+    }
+    const double sg = val < 0.0 ? -1.0 : 1.0;
+    double* Bc = s.B + L * ti(s, TI_RANK)[t0 + warp];
+    for (int i = lane; i < n; i += 32) Bc[i] = sg * x[i];
+  }
+}
+
+// --------------------------------------------------------------------------
+// Eigenvalues with the PD guard (as in the Jacobi route), D, the work counter.
+// --------------------------------------------------------------------------
+constexpr double kTrdPdFloor = 1e-16;
+
+__global__ void __launch_bounds__(kTrdNT) k_trd_finish(Search* S, int s0) {
+  Search& s = S[s0 + blockIdx.x];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const long long L = s.ldn;
+  const double* lams = tv(s, TV_LAMS);
+  const double lo = lams[0], hi = lams[n - 1];
+  const double add = (lo < hi * kTrdPdFloor) ? hi * kTrdPdFloor - lo : 0.0;
+  for (int i = threadIdx.x; i < n; i += kTrdNT) {
+    s.D[i] = sqrt(lams[i] + add);
+    if (add != 0.0) s.C[i + L * i] += add;
+  }
+  if (threadIdx.x == 0) {
+    s.eig_sweeps = 0;
+    s.eig_count += 1;
+  }
+}
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+size_t trd_sytrd_smem(int max_n) { return static_cast<size_t>(3) * max_n * 8; }
+
+int trd_sytrd_blocks_per_sm(int max_n) {
+  int b = 0;
+  const size_t smem = trd_sytrd_smem(max_n);
+  cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trd_sytrd, kTrdNT, smem) != cudaSuccess) {
+    cudaGetLastError();
+    return 0;
+  }
+  return b;
+}
+
+void trd_set_attributes(int max_n) {
+  cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(trd_sytrd_smem(max_n)));
+  cudaFuncSetAttribute(k_trd_backtf, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(trd_bt_smem(max_n)));
+}
+
+// marks (optional, kTrdStages + 1 events): recorded before the reduction and
+// after each stage (reduction, eigenvalues, inverse iteration, Gram-Schmidt in
+// clusters, orthogonalisation, back-transformation), for the per-stage times
+// of the profiling mode.
+int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
+                   int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
+                   TileMap tbt, int max_n, cudaStream_t st, cudaEvent_t* marks) {
+  if (nchunks <= 0 || s1 <= s0) return 0;
+  int nl = 0;
+  auto mark = [&](int k) {
+    if (marks) cudaEventRecord(marks[k], st);
+  };
+  mark(0);
+  cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count, st);
+  for (int c = 0; c < nchunks; ++c) {
+    if (chunks[c].second <= 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(chunks[c].second);
+    cfg.blockDim = dim3(kTrdNT);
+    cfg.dynamicSmemBytes = trd_sytrd_smem(max_n);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_trd_sytrd, S, grp + chunks[c].first);
+    ++nl;
+  }
+  mark(1);
+  k_trd_blocks<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
+  k_trd_bisect<<<tbis.total, kTrdTT, 0, st>>>(S, tbis);
+  k_trd_rank<<<s1 - s0, kTrdSortNT, 0, st>>>(S, s0);
+  mark(2);
+  k_trd_invit<<<tt.total, kTrdTT, 0, st>>>(S, tt);
+  mark(3);
+  k_trd_mgs<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
+  mark(4);
+  for (int pass = 0; pass < kTrdNsSteps; ++pass) {
+    k_trd_gram<<<tsym.total, kGNT, 0, st>>>(S, tsym, pass);
+    k_trd_ns<<<tsq.total, kGNT, 0, st>>>(S, tsq, pass);
+  }
+  mark(5);
+  k_trd_backtf<<<tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tbt);
+  k_trd_finish<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
+  mark(6);
+  return nl + 7 + 2 * kTrdNsSteps;
+}
+
+}  // namespace cmaes_gb300

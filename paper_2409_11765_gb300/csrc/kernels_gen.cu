@@ -115,7 +115,6 @@ __device__ void reset_descent(Search& s) {
     s.gen = 0;
     s.hist_count = 0;
     s.eig_due = 0;
-    s.flags = 0;
   }
 }
 
@@ -129,6 +128,7 @@ __global__ void __launch_bounds__(256) k_init_params(Search* S, int s0, DevOptio
       s.lam = s.lam0;
       s.restart = 0;
       s.done = 0;
+      s.flags = 0;  // a restart keeps the flags that ended the previous descent
       s.best_f = INFINITY;
     }
     __syncthreads();

@@ -86,7 +86,7 @@ __global__ void __cluster_dims__(kCS, 1, 1) __launch_bounds__(512)
   const int crank = static_cast<int>(cl.block_rank());
   Search& s = S[s0 + static_cast<int>(blockIdx.x) / kCS];
   // uniform over the cluster: every CTA reads the same flags
-  if (s.done || !s.eig_due || s.n <= lo_n || s.n > hi_n) return;
+  if (s.done || !s.eig_due || s.trd || s.n <= lo_n || s.n > hi_n) return;
 
   const CLayout L = make_layout(layout_n);
   double* colA = dsm + L.colA;
