@@ -245,7 +245,10 @@ cmaes_status cmaes_best(cmaes_t h, int s, double* x, double* f);
 
 /* Snapshot / restore of search s (see cmaes_state). Synchronises. On restore
  * lambda must lie in [lambda0, lambda0 * 2^max_restarts] (the capacity the
- * search was created with; lambda0 alone when ipop_double = 0). */
+ * search was created with; lambda0 alone when ipop_double = 0), and a finite
+ * sigma must be positive. A non-finite sigma or m is accepted (a checkpoint of
+ * a broken state): the next generation's stop test restarts or ends the
+ * search and the next status read returns CMAES_ENUMERIC once. */
 cmaes_status cmaes_get_state(cmaes_t h, int s, cmaes_state* st);
 cmaes_status cmaes_set_state(cmaes_t h, int s, const cmaes_state* st);
 

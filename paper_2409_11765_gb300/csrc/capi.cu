@@ -55,6 +55,7 @@ struct cmaes_s {
   // tridiagonal route: largest n, the CTA -> (search, member, group size) table
   // of the cooperative reduction, and one barrier counter per search
   int max_n_trd = 0;
+  int trd_bis_lanes = 8;  // lanes per eigenvalue of the multisection (1 for large batches)
   int4* d_trd_grp = nullptr;
   int trd_grp_blocks = 0;
   std::vector<std::pair<int, int>> trd_chunks;  // (first CTA, CTAs) of each cooperative launch
@@ -312,7 +313,8 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
                                   h->d_trd_bar, h->count, s0, s1, h->tiles(TK_TRD, s0, s1),
                                   h->tiles(TK_TRDBIS, s0, s1), h->tiles(TK_TRDSYM, s0, s1),
                                   h->tiles(TK_TRDSQ, s0, s1),
-                                  h->tiles(TK_TRDBT, s0, s1), h->max_n_trd, st, h->trd_marks);
+                                  h->tiles(TK_TRDBT, s0, s1), h->max_n_trd, h->trd_bis_lanes, st,
+                                  h->trd_marks);
     h->launches += nl;
     h->phase_launch[kPhaseEig] += nl;
   }
@@ -810,9 +812,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       if (!x.trd) continue;
       const double share = std::pow(static_cast<double>(x.n), 3.0) / wsum;
       int G = static_cast<int>(std::floor(share * static_cast<double>(spare))) + 1;
-      // at least 32 columns per CTA, and enough work per step to outweigh
-      // the group barrier (n^2 / 32768: one CTA below n = 181)
-      G = std::min(G, std::max(1, std::min(x.n / 32, static_cast<int>(static_cast<long long>(x.n) * x.n / 32768))));
+      // at least 16 columns per CTA, and enough work per step to outweigh
+      // the group barrier (n^2 / 16384: one CTA below n = 181)
+      G = std::min(G, std::max(1, std::min(x.n / 16, static_cast<int>(static_cast<long long>(x.n) * x.n / 16384))));
       if (static_cast<long long>(grp.size()) + G - chunk_start > budget) {
         h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
         chunk_start = static_cast<int>(grp.size());
@@ -821,6 +823,12 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     }
     h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
     h->trd_grp_blocks = static_cast<int>(grp.size());
+    // eigenvalues to find per decomposition of the whole batch: with more than
+    // the GPU holds as 8-lane groups, plain bisection does the least work
+    long long eig_total = 0;
+    for (int s = 0; s < count; ++s)
+      if (h->hs[s].trd) eig_total += h->hs[s].n;
+    h->trd_bis_lanes = eig_total * 8 > static_cast<long long>(sms) * 2048 ? 1 : 8;
     CREATE_TRY(cudaMalloc(&h->d_trd_grp, sizeof(int4) * grp.size()));
     CREATE_TRY(cudaMemcpyAsync(h->d_trd_grp, grp.data(), sizeof(int4) * grp.size(), cudaMemcpyHostToDevice,
                                h->stream));
@@ -1175,7 +1183,9 @@ cmaes_status cmaes_set_state(cmaes_t h, int s, const cmaes_state* st) {
   if (st->lambda < x.lam0 || st->lambda > x.lam_cap)
     return set_error(h, CMAES_EINVAL, "lambda=%d outside [%d, %d]", st->lambda, x.lam0, x.lam_cap);
   if (h->ask_pending[s]) return set_error(h, CMAES_ESTATE, "search %d: ask pending", s);
-  if (st->gen < 0 || st->restart < 0 || st->restart > 255 || !(st->sigma > 0.0))
+  // a non-finite sigma is accepted like a non-finite m (a checkpoint of a
+  // broken state): the next generation's stop test restarts or ends the search
+  if (st->gen < 0 || st->restart < 0 || st->restart > 255 || (std::isfinite(st->sigma) && !(st->sigma > 0.0)))
     return set_error(h, CMAES_EINVAL, "bad gen, restart or sigma");
   const int hist_len = 10 + static_cast<int>(std::ceil(30.0 * x.n / st->lambda));
   if (st->hist_count < 0 || (st->hist_count > 0 && !st->hist))

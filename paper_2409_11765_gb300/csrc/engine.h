@@ -229,6 +229,6 @@ void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
 int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
                    int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
-                   TileMap tbt, int max_n, cudaStream_t st, cudaEvent_t* marks);
+                   TileMap tbt, int max_n, int bis_lanes, cudaStream_t st, cudaEvent_t* marks);
 
 }  // namespace cmaes_gb300

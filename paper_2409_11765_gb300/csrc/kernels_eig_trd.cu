@@ -207,14 +207,42 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_sytrd(Search* S, const int4* grp
       const int j2c = two ? j2 : j1;
       const double vp1 = vprev[j1], wp1 = wprev[j1], vp2 = vprev[j2c], wp2 = wprev[j2c];
       double q1 = 0.0, q2 = 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) {
+      double* W1 = W + L * j1;
+      double* W2 = W + L * j2c;
+      int i = k + 1 + lane;
+      // four rows per lane in flight: the column loads are issued before use
+      for (; i + 96 < n; i += 128) {
+        double a1[4], a2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a1[u] = W1[i + 32 * u];
+          a2[u] = two ? W2[i + 32 * u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int ii = i + 32 * u;
+          const double vi = vprev[ii], wi = wprev[ii], ci = vcur[ii];
+          a1[u] = fma(-wi, vp1, fma(-vi, wp1, a1[u]));
+          q1 = fma(a1[u], ci, q1);
+          if (two) {
+            a2[u] = fma(-wi, vp2, fma(-vi, wp2, a2[u]));
+            q2 = fma(a2[u], ci, q2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          W1[i + 32 * u] = a1[u];
+          if (two) W2[i + 32 * u] = a2[u];
+        }
+      }
+      for (; i < n; i += 32) {
         const double vi = vprev[i], wi = wprev[i], ci = vcur[i];
-        const double a1 = fma(-wi, vp1, fma(-vi, wp1, W[i + L * j1]));
-        W[i + L * j1] = a1;
+        const double a1 = fma(-wi, vp1, fma(-vi, wp1, W1[i]));
+        W1[i] = a1;
         q1 = fma(a1, ci, q1);
         if (two) {
-          const double a2 = fma(-wi, vp2, fma(-vi, wp2, W[i + L * j2]));
-          W[i + L * j2] = a2;
+          const double a2 = fma(-wi, vp2, fma(-vi, wp2, W2[i]));
+          W2[i] = a2;
           q2 = fma(a2, ci, q2);
         }
         if (k == n - 2) d[n - 1] = a1;  // the last diagonal entry (i = j = n - 1)
@@ -344,11 +372,14 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_blocks(Search* S, int s0) {
 }
 
 // --------------------------------------------------------------------------
-// 3. Multisection: a group of 8 lanes finds eigenvalue t - b0 (ascending) of
-// its block; each round the 8 lanes take the Sturm counts at 8 interior points
-// of the bracket, which shrinks it 9-fold. The counts' reciprocals come from
-// an FP32 estimate and two Newton steps in FP64 (exact to rounding) instead of
-// an FP64 divide.
+// 3. Multisection: a group of LANES lanes finds eigenvalue t - b0 (ascending)
+// of its block; each round the lanes take the Sturm counts at LANES interior
+// points of the bracket, which shrinks it (LANES + 1)-fold. Eight lanes cut the
+// sequential rounds from ~52 to ~17 for the few eigenvalues of one search; a
+// large batch, which fills the GPU with eigenvalues anyway, takes one lane
+// (plain bisection: the fewest counts in total). The counts' reciprocals come
+// from an FP32 estimate and two Newton steps in FP64 (exact to rounding)
+// instead of an FP64 divide.
 // --------------------------------------------------------------------------
 constexpr int kTrdTT = 128;   // threads per tile of the per-eigenvalue kernels
 constexpr int kTrdBisLanes = 8;
@@ -365,16 +396,17 @@ __device__ __forceinline__ double fast_rcp(double q) {
   return 1.0 / q;
 }
 
+template <int LANES>
 __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   int tile;
   const int si = find_search(tm, tile);
   const Search& s = S[si];
   if (!trd_due(s)) return;
   const int n = s.n;
-  const int q = threadIdx.x % kTrdBisLanes;
-  const int t = tile * (kTrdTT / kTrdBisLanes) + threadIdx.x / kTrdBisLanes;
-  if (t >= n) return;  // uniform across the 8 lanes of a group
-  const unsigned gmask = 0xFFu << ((threadIdx.x & 31) & ~(kTrdBisLanes - 1));
+  const int q = threadIdx.x % LANES;
+  const int t = tile * (kTrdTT / LANES) + threadIdx.x / LANES;
+  if (t >= n) return;  // uniform across the lanes of a group
+  const unsigned gmask = static_cast<unsigned>((1ull << LANES) - 1) << ((threadIdx.x & 31) & ~(LANES - 1));
   const double* d = tv(s, TV_D);
   const double* es = tv(s, TV_ES);
   const double* e2 = tv(s, TV_E2);
@@ -396,8 +428,8 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   const double fudge = 2.0 * kTrdEps * tn * (b1 - b0) + 2.0 * pivmin;
   double lo = gl - fudge, hi = gu + fudge;
   const int idx = t - b0;
-  for (int it = 0; it < 48 && hi - lo > atol; ++it) {
-    const double w = (hi - lo) / (kTrdBisLanes + 1);
+  for (int it = 0; it < 160 && hi - lo > atol; ++it) {
+    const double w = (hi - lo) / (LANES + 1);
     const double x = lo + w * (q + 1);
     int cnt = 0;
     double qq = d[b0] - x;
@@ -411,10 +443,10 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
     // points with count <= idx lie left of the eigenvalue: the bracket
     // becomes [x_qlo, x_qlo+1] for the rightmost such point qlo
     const unsigned le = __ballot_sync(gmask, cnt <= idx) & gmask;
-    const int base = (threadIdx.x & 31) & ~(kTrdBisLanes - 1);
+    const int base = (threadIdx.x & 31) & ~(LANES - 1);
     const int qlo = le ? (31 - __clz(le)) - base : -1;
     const double nlo = qlo >= 0 ? lo + w * (qlo + 1) : lo;
-    const double nhi = qlo + 1 < kTrdBisLanes ? lo + w * (qlo + 2) : hi;
+    const double nhi = qlo + 1 < LANES ? lo + w * (qlo + 2) : hi;
     if (!(nlo < nhi) || (nlo == lo && nhi == hi)) break;
     lo = nlo;
     hi = nhi;
@@ -546,7 +578,7 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_invit(Search* S, TileMap tm) {
 
 // --------------------------------------------------------------------------
 // 4c. Modified Gram-Schmidt (twice) inside each cluster of close eigenvalues
-// of one block; one warp per cluster, one CTA per search.
+// of one block; one warp per cluster chunk, 16 CTAs per search.
 // --------------------------------------------------------------------------
 // Modified Gram-Schmidt, twice, on vectors [c, ce) of rows [r0, r1) (one warp).
 __device__ void cluster_mgs(double* V, long long L, int c, int ce, int r0, int r1, int lane) {
@@ -577,10 +609,13 @@ __device__ void cluster_mgs(double* V, long long L, int c, int ce, int r0, int r
   }
 }
 
+constexpr int kTrdMgsCtas = 16;  // CTAs per search of the Gram-Schmidt kernel
+
 __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
   Search& s = S[s0 + blockIdx.x];
   if (!trd_due(s)) return;
-  const int n = s.n, lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int n = s.n, lane = threadIdx.x & 31;
+  const int warp = blockIdx.y * (kTrdNT / 32) + (threadIdx.x >> 5);  // of the search's warps
   const long long L = s.ldn;
   const int* cl0 = ti(s, TI_CL0);
   const int* b0a = ti(s, TI_B0);
@@ -589,7 +624,7 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
   int found = 0;
   for (int c = 0; c < n; ++c) {
     if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;  // clusters of two or more
-    if ((found++ % (kTrdNT / 32)) != warp) continue;
+    if ((found++ % (kTrdMgsCtas * kTrdNT / 32)) != warp) continue;
     int ce = c + 1;
     while (ce < n && cl0[ce] == c) ++ce;
     for (int cc = c; cc < ce; cc += kTrdClusMax)
@@ -710,6 +745,7 @@ __global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass
 // the column order of ascending eigenvalues.
 // --------------------------------------------------------------------------
 __host__ __device__ inline int trd_bt_cols(int n) { return n <= 3200 ? 8 : 6; }
+constexpr int kTrdBtRegMaxN = 2048;  // largest n whose columns fit in registers
 int tiles_trd_bt(int n) { return ceil_div(n, trd_bt_cols(n)); }
 size_t trd_bt_smem(int max_n) {
   int best = 0;
@@ -725,6 +761,7 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_backtf(Search* S, TileMap tm) {
   Search& s = S[si];
   if (!trd_due(s)) return;
   const int n = s.n, R = trd_bt_cols(n);
+  if (n <= kTrdBtRegMaxN) return;  // k_trd_backtf_reg takes these sizes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const long long L = s.ldn;
   const int t0 = tile * R;
@@ -772,6 +809,90 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_backtf(Search* S, TileMap tm) {
     const double sg = val < 0.0 ? -1.0 : 1.0;
     double* Bc = s.B + L * ti(s, TI_RANK)[t0 + warp];
     for (int i = lane; i < n; i += 32) Bc[i] = sg * x[i];
+  }
+}
+
+// The same for n <= 32 RMAX with each column held in registers (element
+// lane + 32 r in x[r]): the reflector rows come from L1, the column never
+// moves; rows at or above the reflector's first row are skipped 256 at a time.
+template <int RMAX>
+__global__ void __launch_bounds__(kTrdNT) k_trd_backtf_reg(Search* S, TileMap tm) {
+  int tile;
+  const int si = find_search(tm, tile);
+  Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  if (n > 32 * RMAX || (RMAX > 16 && n <= 16 * RMAX)) return;  // the other variants take these sizes
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+  const int t = tile * trd_bt_cols(n) + warp;
+  if (warp >= trd_bt_cols(n) || t >= n) return;  // warp-uniform; no block barrier below
+  const long long L = s.ldn;
+  const double* Vs = s.EA + L * t;
+  double x[RMAX];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int i = lane + 32 * r;
+    x[r] = i < n ? Vs[i] : 0.0;
+  }
+  const double* tau = tv(s, TV_TAU);
+  const double* Hv = s.EX;
+  constexpr int CH = 8;  // registers per chunk: 256 rows
+  for (int k = n - 2; k >= 0; --k) {
+    const double tk = tau[k];
+    if (tk == 0.0) continue;
+    const double* v = Hv + L * k;
+    double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+    for (int c = 0; c < RMAX / CH; ++c) {
+      if (256 * c + 255 <= k || 256 * c >= n) continue;
+#pragma unroll
+      for (int rr = 0; rr < CH; rr += 2) {
+        const int i0 = lane + 32 * (CH * c + rr), i1 = i0 + 32;
+        if (i0 > k && i0 < n) p0 = fma(v[i0], x[CH * c + rr], p0);
+        if (i1 > k && i1 < n) p1 = fma(v[i1], x[CH * c + rr + 1], p1);
+      }
+    }
+    const double p = tk * warp_sum_xor(p0 + p1);
+#pragma unroll
+    for (int c = 0; c < RMAX / CH; ++c) {
+      if (256 * c + 255 <= k || 256 * c >= n) continue;
+#pragma unroll
+      for (int rr = 0; rr < CH; ++rr) {
+        const int i = lane + 32 * (CH * c + rr);
+        if (i > k && i < n) x[CH * c + rr] = fma(-p, v[i], x[CH * c + rr]);
+      }
+    }
+  }
+  // sign: the entry of largest magnitude (the first on ties) positive
+  double best = -1.0, val = 0.0;
+  int bi = 0x7fffffff;
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int i = lane + 32 * r;
+    const double a = fabs(x[r]);
+    if (i < n && a > best) {
+      best = a;
+      val = x[r];
+      bi = i;
+    }
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const double ob = __shfl_xor_sync(0xffffffffu, best, o);
+    const double ov = __shfl_xor_sync(0xffffffffu, val, o);
+    const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
+    if (ob > best || (ob == best && oi < bi)) {
+      best = ob;
+      val = ov;
+      bi = oi;
+    }
+  }
+  const double sg = val < 0.0 ? -1.0 : 1.0;
+  double* Bc = s.B + L * ti(s, TI_RANK)[t];
+#pragma unroll
+  for (int r = 0; r < RMAX; ++r) {
+    const int i = lane + 32 * r;
+    if (i < n) Bc[i] = sg * x[r];
   }
 }
 
@@ -827,7 +948,7 @@ void trd_set_attributes(int max_n) {
 // of the profiling mode.
 int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
                    int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
-                   TileMap tbt, int max_n, cudaStream_t st, cudaEvent_t* marks) {
+                   TileMap tbt, int max_n, int bis_lanes, cudaStream_t st, cudaEvent_t* marks) {
   if (nchunks <= 0 || s1 <= s0) return 0;
   int nl = 0;
   auto mark = [&](int k) {
@@ -852,22 +973,26 @@ int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks
   }
   mark(1);
   k_trd_blocks<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
-  k_trd_bisect<<<tbis.total, kTrdTT, 0, st>>>(S, tbis);
+  if (bis_lanes > 1) k_trd_bisect<kTrdBisLanes><<<tbis.total, kTrdTT, 0, st>>>(S, tbis);
+  else k_trd_bisect<1><<<tt.total, kTrdTT, 0, st>>>(S, tt);
   k_trd_rank<<<s1 - s0, kTrdSortNT, 0, st>>>(S, s0);
   mark(2);
   k_trd_invit<<<tt.total, kTrdTT, 0, st>>>(S, tt);
   mark(3);
-  k_trd_mgs<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
+  k_trd_mgs<<<dim3(s1 - s0, kTrdMgsCtas), kTrdNT, 0, st>>>(S, s0);
   mark(4);
   for (int pass = 0; pass < kTrdNsSteps; ++pass) {
     k_trd_gram<<<tsym.total, kGNT, 0, st>>>(S, tsym, pass);
     k_trd_ns<<<tsq.total, kGNT, 0, st>>>(S, tsq, pass);
   }
   mark(5);
-  k_trd_backtf<<<tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tbt);
+  k_trd_backtf_reg<16><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // n <= 512
+  k_trd_backtf_reg<32><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // 512 < n <= 1024
+  k_trd_backtf_reg<64><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // 1024 < n <= 2048
+  if (max_n > kTrdBtRegMaxN) k_trd_backtf<<<tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tbt);
   k_trd_finish<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
   mark(6);
-  return nl + 7 + 2 * kTrdNsSteps;
+  return nl + 9 + 2 * kTrdNsSteps + (max_n > kTrdBtRegMaxN ? 1 : 0);
 }
 
 }  // namespace cmaes_gb300

@@ -233,6 +233,7 @@ def test_enumeric_is_reported_once_and_the_handle_stays_usable():
     d = _state(n, 909)
     h = eng.cmaes_create(n, lam, d["m"], 1.0, SEED, eng.cmaes_default_options(max_restarts=3))
     try:
+        eng.cmaes_set_problem(h, 0, eng.OBJ_SPHERE, None, None, np.zeros(n))
         eng.cmaes_set_state(h, 0, dict(n=n, lam=lam, sigma=math.nan, m=d["m"], ps=d["ps"],
                                        pc=d["pc"], C=d["C"], B=d["B"], D=d["D"], gen=1))
         eng.cmaes_step_batch(h, 1)
@@ -253,6 +254,7 @@ def test_injected_device_timeout_is_sticky():
     n, lam = 6, 10
     h = eng.cmaes_create(n, lam, np.zeros(n), 1.0, SEED, eng.cmaes_default_options())
     try:
+        eng.cmaes_set_problem(h, 0, eng.OBJ_SPHERE, None, None, np.ones(n))
         eng.cmaes_step_batch(h, 1)
         eng.cmaes_sync(h)
         # what a tensor-core or barrier wait does when it gives up: the bit in
