@@ -813,10 +813,13 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_backtf(Search* S, TileMap tm) {
 }
 
 // The same for n <= 32 RMAX with each column held in registers (element
-// lane + 32 r in x[r]): the reflector rows come from L1, the column never
-// moves; rows at or above the reflector's first row are skipped 256 at a time.
+// lane + 32 r in x[r]): the column never moves; each reflector is staged once
+// per CTA in shared memory (double-buffered: the next one is loaded while the
+// current one is applied) and rows at or above its first row are skipped 256
+// at a time.
 template <int RMAX>
 __global__ void __launch_bounds__(kTrdNT) k_trd_backtf_reg(Search* S, TileMap tm) {
+  __shared__ double vs[2][32 * RMAX];
   int tile;
   const int si = find_search(tm, tile);
   Search& s = S[si];
@@ -825,44 +828,72 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_backtf_reg(Search* S, TileMap tm
   if (n > 32 * RMAX || (RMAX > 16 && n <= 16 * RMAX)) return;  // the other variants take these sizes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = tile * trd_bt_cols(n) + warp;
-  if (warp >= trd_bt_cols(n) || t >= n) return;  // warp-uniform; no block barrier below
+  const bool active = warp < trd_bt_cols(n) && t < n;  // idle warps still join the barriers
   const long long L = s.ldn;
-  const double* Vs = s.EA + L * t;
+  const double* Vs = s.EA + L * (active ? t : 0);
   double x[RMAX];
 #pragma unroll
   for (int r = 0; r < RMAX; ++r) {
     const int i = lane + 32 * r;
-    x[r] = i < n ? Vs[i] : 0.0;
+    x[r] = (active && i < n) ? Vs[i] : 0.0;
   }
   const double* tau = tv(s, TV_TAU);
   const double* Hv = s.EX;
   constexpr int CH = 8;  // registers per chunk: 256 rows
-  for (int k = n - 2; k >= 0; --k) {
-    const double tk = tau[k];
-    if (tk == 0.0) continue;
-    const double* v = Hv + L * k;
-    double p0 = 0.0, p1 = 0.0;
-#pragma unroll
-    for (int c = 0; c < RMAX / CH; ++c) {
-      if (256 * c + 255 <= k || 256 * c >= n) continue;
-#pragma unroll
-      for (int rr = 0; rr < CH; rr += 2) {
-        const int i0 = lane + 32 * (CH * c + rr), i1 = i0 + 32;
-        if (i0 > k && i0 < n) p0 = fma(v[i0], x[CH * c + rr], p0);
-        if (i1 > k && i1 < n) p1 = fma(v[i1], x[CH * c + rr + 1], p1);
-      }
-    }
-    const double p = tk * warp_sum_xor(p0 + p1);
-#pragma unroll
-    for (int c = 0; c < RMAX / CH; ++c) {
-      if (256 * c + 255 <= k || 256 * c >= n) continue;
-#pragma unroll
-      for (int rr = 0; rr < CH; ++rr) {
-        const int i = lane + 32 * (CH * c + rr);
-        if (i > k && i < n) x[CH * c + rr] = fma(-p, v[i], x[CH * c + rr]);
-      }
-    }
+  // stage reflector k - 1 while k is applied
+  int cur = 0;
+  if (n >= 2) {
+    const double* v0 = Hv + L * (n - 2);
+    for (int i = threadIdx.x; i < n; i += kTrdNT) vs[0][i] = i > n - 2 ? v0[i] : 0.0;
   }
+  __syncthreads();
+  for (int k = n - 2; k >= 0; --k) {
+    // prefetch the next reflector into registers (stored after this one is applied)
+    double pre[(32 * RMAX + kTrdNT - 1) / kTrdNT];
+    if (k > 0) {
+      const double* vn = Hv + L * (k - 1);
+#pragma unroll
+      for (int u = 0; u < (32 * RMAX + kTrdNT - 1) / kTrdNT; ++u) {
+        const int i = threadIdx.x + kTrdNT * u;
+        pre[u] = (i < n && i > k - 1) ? vn[i] : 0.0;
+      }
+    }
+    const double tk = tau[k];
+    const double* v = vs[cur];
+    if (active && tk != 0.0) {
+      double p0 = 0.0, p1 = 0.0;
+#pragma unroll
+      for (int c = 0; c < RMAX / CH; ++c) {
+        if (256 * c + 255 <= k || 256 * c >= n) continue;
+#pragma unroll
+        for (int rr = 0; rr < CH; rr += 2) {
+          const int i0 = lane + 32 * (CH * c + rr), i1 = i0 + 32;
+          if (i0 > k && i0 < n) p0 = fma(v[i0], x[CH * c + rr], p0);
+          if (i1 > k && i1 < n) p1 = fma(v[i1], x[CH * c + rr + 1], p1);
+        }
+      }
+      const double p = tk * warp_sum_xor(p0 + p1);
+#pragma unroll
+      for (int c = 0; c < RMAX / CH; ++c) {
+        if (256 * c + 255 <= k || 256 * c >= n) continue;
+#pragma unroll
+        for (int rr = 0; rr < CH; ++rr) {
+          const int i = lane + 32 * (CH * c + rr);
+          if (i > k && i < n) x[CH * c + rr] = fma(-p, v[i], x[CH * c + rr]);
+        }
+      }
+    }
+    if (k > 0) {
+#pragma unroll
+      for (int u = 0; u < (32 * RMAX + kTrdNT - 1) / kTrdNT; ++u) {
+        const int i = threadIdx.x + kTrdNT * u;
+        if (i < 32 * RMAX) vs[cur ^ 1][i] = pre[u];
+      }
+    }
+    __syncthreads();
+    cur ^= 1;
+  }
+  if (!active) return;
   // sign: the entry of largest magnitude (the first on ties) positive
   double best = -1.0, val = 0.0;
   int bi = 0x7fffffff;
