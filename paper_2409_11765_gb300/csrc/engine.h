@@ -88,7 +88,7 @@ struct Search {
   // tridiagonal route of the eigendecomposition (kernels_eig_trd.cu)
   int trd, trd_pad_;  // 1: this search's eigendecomposition takes the tridiagonal route
   double* trd_v;      // 11 x ldn doubles: d, e, split e, e^2, tau, eigenvalues (two orders), p and p.v buffers, scalars
-  int* trd_i;         // 4 x ldn ints: block start / end, rank, cluster start
+  int* trd_i;         // 5 x ldn ints: block start / end, rank, cluster start, V^T V tile flags
   unsigned* trd_bar;  // the group barrier counter of the reduction
 };
 
@@ -217,7 +217,7 @@ void set_global_error(const char* msg);
 // CTA's shared memory, is faster)
 constexpr int kEigAutoTrdN = kEigMixedMaxN;
 constexpr int kTrdVectors = 11;  // Search::trd_v, in ldn doubles
-constexpr int kTrdInts = 4;      // Search::trd_i, in ldn ints
+constexpr int kTrdInts = 5;      // Search::trd_i, in ldn ints
 int tiles_trd(int n);      // 128 eigenvalues per tile
 int tiles_trd_bis(int n);  // 16 eigenvalues per tile (8 lanes each)
 int tiles_trd_sym(int n);  // upper 64 x 64 tiles of n x n

@@ -56,7 +56,7 @@ namespace cmaes_gb300 {
 // alternate between ET and EA and end in EA.
 // --------------------------------------------------------------------------
 enum { TV_D = 0, TV_E, TV_ES, TV_E2, TV_TAU, TV_LAMB, TV_LAMS, TV_P0, TV_P1, TV_SD, TV_SCAL };
-enum { TI_B0 = 0, TI_B1, TI_RANK, TI_CL0 };
+enum { TI_B0 = 0, TI_B1, TI_RANK, TI_CL0, TI_TFLAG };
 // scalars at TV_SCAL: ||T|| bound, pivmin, split threshold, cluster threshold,
 // and the orthogonality defect max |(I - V^T V) / 2| before each Newton-Schulz
 // step (as ordered bit patterns for atomicMax)
@@ -65,6 +65,10 @@ constexpr double kTrdClus = 1e-13;
 constexpr int kTrdClusMax = 64;      // Gram-Schmidt chunk of a longer cluster
 constexpr int kTrdNsSteps = 3;
 constexpr double kTrdNsSkip = 5e-9;  // one step leaves 1.5 (2 * 5e-9)^2 < eps64
+// V^T V is formed only for 64 x 64 tiles holding a pair of vectors of one
+// block whose eigenvalues lie within kTrdNsBand ||T||: for a pair further apart
+// inverse iteration already leaves |v_i^T v_j| <~ eps64 / kTrdNsBand ~ 1e-14.
+constexpr double kTrdNsBand = 1e-2;
 constexpr double kTrdEps = 0x1p-53;
 constexpr long long kTrdWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
 constexpr int kTrdNT = 256;
@@ -634,7 +638,8 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
 
 // --------------------------------------------------------------------------
 // 5. Newton-Schulz: M = (I - V^T V) / 2 in FP32 from an FP64 product (upper
-// 64 x 64 tiles, mirrored), then V' = V + V M with FP32 products (all tiles).
+// 64 x 64 tiles, mirrored; tiles outside the eigenvalue band are zero and
+// flagged so), then V' = V + V M with FP32 products over the nonzero tiles.
 // --------------------------------------------------------------------------
 int tiles_trd_sym(int n) { const int T = ceil_div(n, kGBM); return T * (T + 1) / 2; }
 int tiles_trd_sq(int n) { const int T = ceil_div(n, kGBM); return T * T; }
@@ -657,6 +662,59 @@ __global__ void __launch_bounds__(kGNT) k_trd_gram(Search* S, TileMap tm, int pa
   const long long L = s.ldn;
   const double* V = (pass & 1) ? s.EA : s.ET;
   float* M = reinterpret_cast<float*>(s.EG);
+  int* flags = ti(s, TI_TFLAG);
+  // band test: do the two tiles hold a pair of one block with eigenvalues
+  // within kTrdNsBand ||T|| of each other? (block starts and, inside a block,
+  // eigenvalues ascend with the column index)
+  __shared__ double trange[4];
+  __shared__ int brange[4];
+  if (threadIdx.x < 64) {
+    const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
+    const int c0 = (w == 0 ? bi : bj) * kGBM;
+    double lo = INFINITY, hi = -INFINITY;
+    int blo = 0x7fffffff, bhi = -1;
+    for (int u = l; u < kGBM; u += 32) {
+      const int t = c0 + u;
+      if (t < n) {
+        const double lam = tv(s, TV_LAMB)[t];
+        const int b = ti(s, TI_B0)[t];
+        lo = fmin(lo, lam);
+        hi = fmax(hi, lam);
+        blo = min(blo, b);
+        bhi = max(bhi, b);
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      lo = fmin(lo, __shfl_xor_sync(0xffffffffu, lo, o));
+      hi = fmax(hi, __shfl_xor_sync(0xffffffffu, hi, o));
+      blo = min(blo, __shfl_xor_sync(0xffffffffu, blo, o));
+      bhi = max(bhi, __shfl_xor_sync(0xffffffffu, bhi, o));
+    }
+    if (l == 0) {
+      trange[2 * w] = lo;
+      trange[2 * w + 1] = hi;
+      brange[2 * w] = blo;
+      brange[2 * w + 1] = bhi;
+    }
+  }
+  __syncthreads();
+  const bool share_block = brange[0] <= brange[3] && brange[2] <= brange[1];
+  const double dist = fmax(0.0, fmax(trange[2] - trange[1], trange[0] - trange[3]));
+  const bool needed = share_block && !(dist > kTrdNsBand * sc[0]);
+  if (threadIdx.x == 0) {
+    flags[bi + T * bj] = needed;
+    flags[bj + T * bi] = needed;
+  }
+  if (!needed) {  // M = 0 on this tile and its mirror
+    for (int e = threadIdx.x; e < kGBM * kGBN; e += kGNT) {
+      const int i = bi * kGBM + (e & (kGBM - 1)), j = bj * kGBN + e / kGBM;
+      if (i < n && j < n) {
+        M[i + L * j] = 0.f;
+        M[j + L * i] = 0.f;
+      }
+    }
+    return;
+  }
   double dmax = 0.0;
   gemm_tile_f64<false, true>(
       n, n, n, bi * kGBM, bj * kGBN, [=] __device__(int i, int k) { return V[k + L * i]; },
@@ -703,8 +761,10 @@ __global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass
     return;
   }
   const float* M = reinterpret_cast<const float*>(s.EG);
+  const int* flags = ti(s, TI_TFLAG);
   float acc[4][4] = {};
   for (int k0 = 0; k0 < n; k0 += kGBK) {
+    if (!__ldcg(&flags[k0 / kGBM + T * (j0 / kGBN)])) continue;  // M is zero on this tile
 #pragma unroll
     for (int q = 0; q < 4; ++q) {
       const int e = tid + q * kGNT;
