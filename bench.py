@@ -42,7 +42,7 @@ if ROOT not in sys.path:
 METRIC = "candidates/sec sampled+evaluated+updated; mixed vs plain FP64 GPU; % roofline"
 UNIT = "candidates/s"
 SEED = 20240918
-WORKLOADS = ("batch256", "rastrigin-n100-kdist", "ellipsoid-n1000", "ellipsoid-n4096",
+WORKLOADS = ("batch256", "batch32", "rastrigin-n100-kdist", "ellipsoid-n1000", "ellipsoid-n4096",
              "ellipsoid-n10", "rastrigin-n100-ipop")
 
 
@@ -75,6 +75,8 @@ def workload(name):
     from paper_2409_11765_gb300 import workloads as W
     if name == "batch256":
         return W.batch256()
+    if name == "batch32":
+        return W.batch32()
     if name == "rastrigin-n100-kdist":
         return W.rastrigin_n100_ipop(concurrent=True)
     if name == "rastrigin-n100-ipop":

@@ -170,6 +170,15 @@ def batch256(seed=SEED, count=256):
                     notes="K-Distributed: 256 searches of uneven (n, lambda) in one batch")
 
 
+def batch32(seed=SEED):
+    """The first 32 searches of the 256-search batch (the same shapes, problems
+    and starts): a case small enough for detailed counter captures whose
+    eigensolver matrices (144 MB) still exceed the GPU's L2."""
+    wl = batch256(seed, count=32)
+    wl.name = "batch256-first32"
+    return wl
+
+
 def ellipsoid_n4096(seed=SEED, kind=ELLIPSOID):
     """Large scale: n=4096, lambda=8192, rotated ellipsoid cond 1e4 (or the
     separable sphere control)."""
