@@ -23,7 +23,7 @@ __all__ = [
     "cmaes_set_profiling", "cmaes_phase_times", "cmaes_kernel_launches", "cmaes_eig_stats",
     "cmaes_eig_stage_times",
     "cmaes_ask_async", "cmaes_tell_async",
-    "probe_fma_tflops", "cmaes_evaluate_noalloc", "cmaes_inject_status", "cmaes_strerror",
+    "probe_fma_tflops", "cmaes_ozaki_dgemm", "cmaes_evaluate_noalloc", "cmaes_inject_status", "cmaes_strerror",
     "cmaes_last_error", "cmaes_destroy",
 ]
 
@@ -111,6 +111,8 @@ def lib():
         "cmaes_ask_async": (I, [H, I, I, ctypes.POINTER(V), ctypes.POINTER(ctypes.c_int), V]),
         "cmaes_tell_async": (I, [H, I, I, ctypes.POINTER(V), V]),
         "cmaes_inject_status": (I, [H, I]),
+        "cmaes_ozaki_dgemm": (I, [I, I, I, D, V, ctypes.c_longlong, V, ctypes.c_longlong, D, V,
+                                  ctypes.c_longlong, V]),
         "cmaes_strerror": (ctypes.c_char_p, [I]),
         "cmaes_last_error": (ctypes.c_char_p, [H]),
         "cmaes_destroy": (None, [H]),
@@ -345,6 +347,15 @@ def probe_fma_tflops(precision=64, blocks_per_sm=4, repeats=5):
     if st != 0:
         raise CmaesError(st, "FMA probe failed")
     return out.value
+
+
+def cmaes_ozaki_dgemm(M, N, K, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream=None):
+    """C = alpha A B + beta C on device arrays (pointers as ints, column-major)
+    with the engine's FP64-accurate tensor-core product; see
+    include/cmaes_ozaki.h."""
+    st = lib().cmaes_ozaki_dgemm(M, N, K, alpha, A_ptr, lda, B_ptr, ldb, beta, C_ptr, ldc, stream)
+    if st != 0:
+        raise CmaesError({1: 1, 2: 2, 3: 3, 4: 5}.get(st, 3), "cmaes_ozaki_dgemm returned %d" % st)
 
 
 def cmaes_kernel_launches(h):
