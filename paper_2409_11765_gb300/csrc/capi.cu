@@ -309,11 +309,10 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
     // the cooperative reduction always covers every search of the handle (its
     // group table is fixed at create); the searches outside [s0, s1) that
     // are due are reduced too, which only repeats their decomposition
+    const TrdMaps tmaps{h->tiles(TK_TRD, s0, s1),   h->tiles(TK_TRDBIS, s0, s1), h->tiles(TK_TRDSQ, s0, s1),
+                        h->tiles(TK_TRDBT, s0, s1), h->tiles(TK_TRDOZP, s0, s1), h->tiles(TK_TRDOZG, s0, s1)};
     const int nl = launch_eig_trd(h->dS, h->d_trd_grp, h->trd_chunks.data(), static_cast<int>(h->trd_chunks.size()),
-                                  h->d_trd_bar, h->count, s0, s1, h->tiles(TK_TRD, s0, s1),
-                                  h->tiles(TK_TRDBIS, s0, s1), h->tiles(TK_TRDSYM, s0, s1),
-                                  h->tiles(TK_TRDSQ, s0, s1),
-                                  h->tiles(TK_TRDBT, s0, s1), h->max_n_trd, h->trd_bis_lanes, st,
+                                  h->d_trd_bar, h->count, s0, s1, tmaps, h->max_n_trd, h->trd_bis_lanes, st,
                                   h->trd_marks);
     h->launches += nl;
     h->phase_launch[kPhaseEig] += nl;
@@ -661,7 +660,9 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * jlog_pairs(n) * 8);  // jlog
       b += align256(static_cast<size_t>(jlog_steps_cap(n)) * 4);                  // jlog_r
     }
-    if (x.trd) b += align256(ldn * kTrdVectors * 8) + align256(ldn * kTrdInts * 4);
+    if (x.trd)
+      b += align256(ldn * kTrdVectors * 8) + align256(ldn * kTrdInts * 4) + align256(trd_oz_bytes(n)) +
+           align256(static_cast<size_t>(trd_oz_exps(n)) * 4);
     if (eig_big_route(n) && !x.trd) {
       b += align256(jb_buf_floats(n) * 4);                         // jb_buf
       b += align256(static_cast<size_t>(jlog_pairs(n)) * 16);      // jb_rec
@@ -754,6 +755,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     if (x.trd) {
       x.trd_v = reinterpret_cast<double*>(take(ldn * kTrdVectors * 8));
       x.trd_i = reinterpret_cast<int*>(take(ldn * kTrdInts * 4));
+      x.ozp = reinterpret_cast<unsigned char*>(take(trd_oz_bytes(x.n)));
+      x.oze = reinterpret_cast<int*>(take(static_cast<size_t>(trd_oz_exps(x.n)) * 4));
     }
     if (eig_big_route(x.n) && !x.trd) {
       x.jb_buf = reinterpret_cast<float*>(take(jb_buf_floats(x.n) * 4));
@@ -865,9 +868,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_FLATSYM: t = eig_refined_route(x) ? tiles_flat_sym(x.n) : 0; break;
         case TK_TRD: t = x.trd ? tiles_trd(x.n) : 0; break;
         case TK_TRDBIS: t = x.trd ? tiles_trd_bis(x.n) : 0; break;
-        case TK_TRDSYM: t = x.trd ? tiles_trd_sym(x.n) : 0; break;
         case TK_TRDSQ: t = x.trd ? tiles_trd_sq(x.n) : 0; break;
         case TK_TRDBT: t = x.trd ? tiles_trd_bt(x.n) : 0; break;
+        case TK_TRDOZP: t = x.trd ? tiles_trd_ozp(x.n) : 0; break;
+        case TK_TRDOZG: t = x.trd ? tiles_trd_ozg(x.n) : 0; break;
         case TK_JBBLK: t = x.trd ? 0 : tiles_jb_blocks(x.n); break;
         case TK_JBLOAD: t = x.trd ? 0 : tiles_jb_load(x.n); break;
         case TK_JBROWS: t = x.trd ? 0 : tiles_jb_rows(x.n); break;

@@ -90,6 +90,8 @@ struct Search {
   double* trd_v;      // 11 x ldn doubles: d, e, split e, e^2, tau, eigenvalues (two orders), p and p.v buffers, scalars
   int* trd_i;         // 5 x ldn ints: block start / end, rank, cluster start, V^T V tile flags
   unsigned* trd_bar;  // the group barrier counter of the reduction
+  unsigned char* ozp; // packed digit planes of the FP64-accurate tensor-core products (trd_oz_bytes)
+  int* oze;           // their row exponents (trd_oz_exps ints)
 };
 
 // Flattened tiles of one kernel over a contiguous range of searches:
@@ -118,7 +120,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_TRD, TK_TRDBIS, TK_TRDSYM, TK_TRDSQ, TK_TRDBT, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -220,15 +222,21 @@ constexpr int kTrdVectors = 11;  // Search::trd_v, in ldn doubles
 constexpr int kTrdInts = 5;      // Search::trd_i, in ldn ints
 int tiles_trd(int n);      // 128 eigenvalues per tile
 int tiles_trd_bis(int n);  // 16 eigenvalues per tile (8 lanes each)
-int tiles_trd_sym(int n);  // upper 64 x 64 tiles of n x n
 int tiles_trd_sq(int n);   // all 64 x 64 tiles of n x n
 int tiles_trd_bt(int n);   // column groups of the back-transformation
+int tiles_trd_ozp(int n);  // 64-row blocks of a packed n x n operand
+int tiles_trd_ozg(int n);  // 128 x 64 tiles of the Gram matrix V^T V
+size_t trd_oz_bytes(int n);  // Search::ozp
+int trd_oz_exps(int n);      // Search::oze
 size_t trd_sytrd_smem(int max_n);
 int trd_sytrd_blocks_per_sm(int max_n);
 void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
+struct TrdMaps {
+  TileMap tt, tbis, tsq, tbt, ozp, ozg;  // TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG
+};
 int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
-                   int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
-                   TileMap tbt, int max_n, int bis_lanes, cudaStream_t st, cudaEvent_t* marks);
+                   int bar_count, int s0, int s1, const TrdMaps& tm, int max_n, int bis_lanes, cudaStream_t st,
+                   cudaEvent_t* marks);
 
 }  // namespace cmaes_gb300

@@ -44,6 +44,7 @@
 #include <cfloat>
 #include <cmath>
 #include "device_common.cuh"
+#include "ozaki.cuh"
 
 namespace cmaes_gb300 {
 
@@ -637,40 +638,60 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
 }
 
 // --------------------------------------------------------------------------
-// 5. Newton-Schulz: M = (I - V^T V) / 2 in FP32 from an FP64 product (upper
-// 64 x 64 tiles, mirrored; tiles outside the eigenvalue band are zero and
-// flagged so), then V' = V + V M with FP32 products over the nonzero tiles.
+// 5. Newton-Schulz: M = (I - V^T V) / 2 in FP32 from an FP64-accurate
+// product on the tensor cores (64 x 64 tiles, mirrored; tiles outside the
+// eigenvalue band are zero and flagged so), then V' = V + V M with FP32
+// products over the nonzero tiles.
 // --------------------------------------------------------------------------
-int tiles_trd_sym(int n) { const int T = ceil_div(n, kGBM); return T * (T + 1) / 2; }
 int tiles_trd_sq(int n) { const int T = ceil_div(n, kGBM); return T * T; }
 
-__global__ void __launch_bounds__(kGNT) k_trd_gram(Search* S, TileMap tm, int pass) {
-  __shared__ GemmSmem sm;
+int tiles_trd_ozp(int n) { return oz_rows_padded(n) / 64; }
+int tiles_trd_ozg(int n) { return ceil_div(n, kOzBM) * ceil_div(n, kOzBN); }
+size_t trd_oz_bytes(int n) { return oz_bytes(n, n); }
+int trd_oz_exps(int n) { return 4 * oz_rows_padded(n); }
+
+__device__ __forceinline__ bool trd_ns_skipped(const Search& s, int pass) {
+  return pass > 0 && __ldcg(&tv(s, TV_SCAL)[3 + pass]) <= kTrdNsSkip;  // the previous step was enough
+}
+
+// The columns of this pass's V as the rows of a packed operand (K = n).
+__global__ void __launch_bounds__(kOzNT) k_trd_oz_pack(Search* S, TileMap tm, int pass) {
+  __shared__ int sh_e[64];
   int tile;
   const int si = find_search(tm, tile);
   const Search& s = S[si];
-  if (!trd_due(s)) return;
-  double* sc = tv(s, TV_SCAL);
-  if (pass > 0 && __ldcg(&sc[3 + pass]) <= kTrdNsSkip) return;  // the previous step was enough
-  const int n = s.n, T = ceil_div(n, kGBM);
-  int bi = 0, rem = tile;  // upper tiles, row-block major: (bi, bj) with bj >= bi
-  while (rem >= T - bi) {
-    rem -= T - bi;
-    ++bi;
-  }
-  const int bj = bi + rem;
-  const long long L = s.ldn;
+  if (!trd_due(s) || trd_ns_skipped(s, pass)) return;
   const double* V = (pass & 1) ? s.EA : s.ET;
+  oz_pack_block(V, s.ldn, 1, s.n, s.n, tile, oz_nks(s.n), s.ozp, s.oze, sh_e);
+}
+
+// M = (I - V^T V) / 2 over the 64 x 64 tiles (fi, fj), fi <= fj, that hold a
+// pair of one block with eigenvalues within kTrdNsBand ||T|| (mirrored,
+// flagged; zero and unflagged elsewhere), from the FP64-accurate tensor-core
+// product: CTA (bi, bj) owns the 128 x 64 tile of rows 128 bi.., columns
+// 64 bj.., i.e. the 64 x 64 tiles (2 bi, bj) and (2 bi + 1, bj), and writes
+// the elements i <= j of those it owns.
+__global__ void __launch_bounds__(kOzNT, 1) k_trd_oz_gram(Search* S, TileMap tm, int pass) {
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t bar[5];
+  __shared__ uint32_t tslot;
+  __shared__ double trange[3][2];
+  __shared__ int brange[3][2];
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s) || trd_ns_skipped(s, pass)) return;
+  const int n = s.n, T = ceil_div(n, kGBM), TN = ceil_div(n, kOzBN);
+  const int bi = tile / TN, bj = tile % TN;
+  if (bj * kOzBN + kOzBN - 1 < bi * kOzBM) return;  // wholly below the diagonal
+  const long long L = s.ldn;
   float* M = reinterpret_cast<float*>(s.EG);
   int* flags = ti(s, TI_TFLAG);
-  // band test: do the two tiles hold a pair of one block with eigenvalues
-  // within kTrdNsBand ||T|| of each other? (block starts and, inside a block,
-  // eigenvalues ascend with the column index)
-  __shared__ double trange[4];
-  __shared__ int brange[4];
-  if (threadIdx.x < 64) {
+  double* sc = tv(s, TV_SCAL);
+  // eigenvalue and block ranges of the column blocks 2 bi, 2 bi + 1 and bj
+  if (threadIdx.x < 96) {
     const int w = threadIdx.x >> 5, l = threadIdx.x & 31;
-    const int c0 = (w == 0 ? bi : bj) * kGBM;
+    const int c0 = (w == 0 ? 2 * bi : (w == 1 ? 2 * bi + 1 : bj)) * kGBM;
     double lo = INFINITY, hi = -INFINITY;
     int blo = 0x7fffffff, bhi = -1;
     for (int u = l; u < kGBM; u += 32) {
@@ -691,46 +712,75 @@ __global__ void __launch_bounds__(kGNT) k_trd_gram(Search* S, TileMap tm, int pa
       bhi = max(bhi, __shfl_xor_sync(0xffffffffu, bhi, o));
     }
     if (l == 0) {
-      trange[2 * w] = lo;
-      trange[2 * w + 1] = hi;
-      brange[2 * w] = blo;
-      brange[2 * w + 1] = bhi;
+      trange[w][0] = lo;
+      trange[w][1] = hi;
+      brange[w][0] = blo;
+      brange[w][1] = bhi;
     }
   }
   __syncthreads();
-  const bool share_block = brange[0] <= brange[3] && brange[2] <= brange[1];
-  const double dist = fmax(0.0, fmax(trange[2] - trange[1], trange[0] - trange[3]));
-  const bool needed = share_block && !(dist > kTrdNsBand * sc[0]);
-  if (threadIdx.x == 0) {
-    flags[bi + T * bj] = needed;
-    flags[bj + T * bi] = needed;
-  }
-  if (!needed) {  // M = 0 on this tile and its mirror
-    for (int e = threadIdx.x; e < kGBM * kGBN; e += kGNT) {
-      const int i = bi * kGBM + (e & (kGBM - 1)), j = bj * kGBN + e / kGBM;
-      if (i < n && j < n) {
-        M[i + L * j] = 0.f;
-        M[j + L * i] = 0.f;
-      }
+  bool owned[2], needed[2];
+#pragma unroll
+  for (int h = 0; h < 2; ++h) {
+    const int fi = 2 * bi + h;
+    owned[h] = fi <= bj && fi < T;
+    const bool share = brange[h][0] <= brange[2][1] && brange[2][0] <= brange[h][1];
+    const double dist = fmax(0.0, fmax(trange[2][0] - trange[h][1], trange[h][0] - trange[2][1]));
+    needed[h] = owned[h] && share && !(dist > kTrdNsBand * sc[0]);
+    if (owned[h] && threadIdx.x == 0) {
+      flags[fi + T * bj] = needed[h];
+      flags[bj + T * fi] = needed[h];
     }
+  }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = bi * kOzBM + 32 * (warp & 3) + lane;
+  const int h = (warp & 3) >> 1;
+  const int jb = bj * kOzBN + 32 * (warp >> 2);
+  if (!needed[0] && !needed[1]) {  // M = 0 on the owned tiles and their mirrors
+    if (owned[h] && i < n)
+      for (int q = 0; q < 32; ++q) {
+        const int j = jb + q;
+        if (j < n && i <= j) {
+          M[i + L * j] = 0.f;
+          M[j + L * i] = 0.f;
+        }
+      }
     return;
   }
+  OzCtx cx;
+  oz_begin(cx, dyn, bar, &tslot);
+  long long Wq[32];
+  float Lq[32];
+  const long long pitch = oz_pitch(oz_nks(n));
+  const bool ok = oz_tile(cx, s.ozp, pitch, 2 * bi, s.ozp, pitch, bj, oz_nks(n), Wq, Lq);
   double dmax = 0.0;
-  gemm_tile_f64<false, true>(
-      n, n, n, bi * kGBM, bj * kGBN, [=] __device__(int i, int k) { return V[k + L * i]; },
-      [=] __device__(int k, int j) { return V[k + L * j]; },
-      [&] __device__(int i, int j, double g) {
-        const double m = 0.5 * ((i == j ? 1.0 : 0.0) - g);
+  if (ok && owned[h] && i < n) {
+    const int ei = s.oze[i];
+#pragma unroll
+    for (int q = 0; q < 32; ++q) {
+      const int j = jb + q;
+      if (j < n && i <= j) {
+        double m = 0.0;
+        if (needed[h]) {
+          const int ej = s.oze[j];
+          double g = (static_cast<double>(Wq[q]) + static_cast<double>(Lq[q])) * oz_pow2(ei + ej - 44);
+          if (ei <= kOzZeroExp || ej <= kOzZeroExp) g = 0.0;
+          m = 0.5 * ((i == j ? 1.0 : 0.0) - g);
+          dmax = fmax(dmax, fabs(m));
+        }
         M[i + L * j] = static_cast<float>(m);
         M[j + L * i] = static_cast<float>(m);
-        dmax = fmax(dmax, fabs(m));
-      },
-      sm);
-  // the defect of this pass (non-negative doubles order like their bit patterns)
+      }
+    }
+  }
+  // the defect of this pass (non-negative doubles order like their bit
+  // patterns); every lane of every warp takes part in the reduction
   for (int o = 16; o > 0; o >>= 1) dmax = fmax(dmax, __shfl_xor_sync(0xffffffffu, dmax, o));
-  if ((threadIdx.x & 31) == 0 && dmax > 0.0)
+  if (lane == 0 && dmax > 0.0)
     atomicMax(reinterpret_cast<unsigned long long*>(&sc[4 + pass]),
               static_cast<unsigned long long>(__double_as_longlong(dmax)));
+  if (!ok && threadIdx.x == 0) atomicOr(s.err, kDevErrTimeout);
+  oz_end(cx);
 }
 
 struct GemmSmem32 {
@@ -1031,6 +1081,7 @@ void trd_set_attributes(int max_n) {
                        static_cast<int>(trd_sytrd_smem(max_n)));
   cudaFuncSetAttribute(k_trd_backtf, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(trd_bt_smem(max_n)));
+  cudaFuncSetAttribute(k_trd_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
 }
 
 // marks (optional, kTrdStages + 1 events): recorded before the reduction and
@@ -1038,8 +1089,8 @@ void trd_set_attributes(int max_n) {
 // clusters, orthogonalisation, back-transformation), for the per-stage times
 // of the profiling mode.
 int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
-                   int bar_count, int s0, int s1, TileMap tt, TileMap tbis, TileMap tsym, TileMap tsq,
-                   TileMap tbt, int max_n, int bis_lanes, cudaStream_t st, cudaEvent_t* marks) {
+                   int bar_count, int s0, int s1, const TrdMaps& tm, int max_n, int bis_lanes, cudaStream_t st,
+                   cudaEvent_t* marks) {
   if (nchunks <= 0 || s1 <= s0) return 0;
   int nl = 0;
   auto mark = [&](int k) {
@@ -1064,26 +1115,27 @@ int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks
   }
   mark(1);
   k_trd_blocks<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
-  if (bis_lanes > 1) k_trd_bisect<kTrdBisLanes><<<tbis.total, kTrdTT, 0, st>>>(S, tbis);
-  else k_trd_bisect<1><<<tt.total, kTrdTT, 0, st>>>(S, tt);
+  if (bis_lanes > 1) k_trd_bisect<kTrdBisLanes><<<tm.tbis.total, kTrdTT, 0, st>>>(S, tm.tbis);
+  else k_trd_bisect<1><<<tm.tt.total, kTrdTT, 0, st>>>(S, tm.tt);
   k_trd_rank<<<s1 - s0, kTrdSortNT, 0, st>>>(S, s0);
   mark(2);
-  k_trd_invit<<<tt.total, kTrdTT, 0, st>>>(S, tt);
+  k_trd_invit<<<tm.tt.total, kTrdTT, 0, st>>>(S, tm.tt);
   mark(3);
   k_trd_mgs<<<dim3(s1 - s0, kTrdMgsCtas), kTrdNT, 0, st>>>(S, s0);
   mark(4);
   for (int pass = 0; pass < kTrdNsSteps; ++pass) {
-    k_trd_gram<<<tsym.total, kGNT, 0, st>>>(S, tsym, pass);
-    k_trd_ns<<<tsq.total, kGNT, 0, st>>>(S, tsq, pass);
+    if (tm.ozp.total > 0) k_trd_oz_pack<<<tm.ozp.total, kOzNT, 0, st>>>(S, tm.ozp, pass);
+    if (tm.ozg.total > 0) k_trd_oz_gram<<<tm.ozg.total, kOzNT, kOzSmem, st>>>(S, tm.ozg, pass);
+    k_trd_ns<<<tm.tsq.total, kGNT, 0, st>>>(S, tm.tsq, pass);
   }
   mark(5);
-  k_trd_backtf_reg<16><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // n <= 512
-  k_trd_backtf_reg<32><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // 512 < n <= 1024
-  k_trd_backtf_reg<64><<<tbt.total, kTrdNT, 0, st>>>(S, tbt);   // 1024 < n <= 2048
-  if (max_n > kTrdBtRegMaxN) k_trd_backtf<<<tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tbt);
+  k_trd_backtf_reg<16><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // n <= 512
+  k_trd_backtf_reg<32><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // 512 < n <= 1024
+  k_trd_backtf_reg<64><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // 1024 < n <= 2048
+  if (max_n > kTrdBtRegMaxN) k_trd_backtf<<<tm.tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tm.tbt);
   k_trd_finish<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
   mark(6);
-  return nl + 9 + 2 * kTrdNsSteps + (max_n > kTrdBtRegMaxN ? 1 : 0);
+  return nl + 9 + 3 * kTrdNsSteps + (max_n > kTrdBtRegMaxN ? 1 : 0);
 }
 
 }  // namespace cmaes_gb300

@@ -231,7 +231,7 @@ __device__ __forceinline__ void oz_end(OzCtx& cx) {
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" :: "r"(cx.tmem), "r"(kOzTmemCols));
 }
 
-__device__ bool oz_tile(OzCtx& cx, const unsigned char* __restrict__ A, long long a_pitch, int a_rb,
+__device__ __forceinline__ bool oz_tile(OzCtx& cx, const unsigned char* __restrict__ A, long long a_pitch, int a_rb,
                         const unsigned char* __restrict__ B, long long b_pitch, int b_rb, int nks,
                         long long (&W)[32], float (&L)[32]) {
   const int tid = threadIdx.x, warp = tid >> 5;
