@@ -11,7 +11,7 @@ LIB = os.path.join(LIBDIR, "libcmaes_gb300.so")
 PROBE_LIB = os.path.join(LIBDIR, "libcmaes_probe.so")
 INCLUDE = os.path.join(os.path.dirname(PKG), "include")
 SOURCES = ["kernels_gen.cu", "kernels_eig.cu", "kernels_jacobi_cluster.cu", "kernels_mixed.cu",
-           "kernels_eig_mixed.cu", "kernels_eig_big.cu", "kernels_eig_trd.cu", "kernels_ozaki.cu", "capi.cu", "noalloc.cu"]
+           "kernels_eig_mixed.cu", "kernels_eig_big.cu", "kernels_eig_trd.cu", "kernels_eig_trd_bt.cu", "kernels_ozaki.cu", "capi.cu", "noalloc.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-std=c++17", "--extended-lambda", "-O3", "-lineinfo", "-Xcompiler", "-fPIC",
          "-Xcompiler", "-O2"]

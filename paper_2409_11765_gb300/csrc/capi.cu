@@ -310,7 +310,10 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
     // group table is fixed at create); the searches outside [s0, s1) that
     // are due are reduced too, which only repeats their decomposition
     const TrdMaps tmaps{h->tiles(TK_TRD, s0, s1),   h->tiles(TK_TRDBIS, s0, s1), h->tiles(TK_TRDSQ, s0, s1),
-                        h->tiles(TK_TRDBT, s0, s1), h->tiles(TK_TRDOZP, s0, s1), h->tiles(TK_TRDOZG, s0, s1)};
+                        h->tiles(TK_TRDBT, s0, s1), h->tiles(TK_TRDOZP, s0, s1), h->tiles(TK_TRDOZG, s0, s1),
+                        h->tiles(TK_BTPACK, s0, s1), h->tiles(TK_BTGRAM, s0, s1), h->tiles(TK_BTTFAC, s0, s1),
+                        h->tiles(TK_BTROWS, s0, s1), h->tiles(TK_BTCOLS, s0, s1), h->tiles(TK_BTUPD, s0, s1),
+                        h->tiles(TK_BTFIN, s0, s1)};
     const int nl = launch_eig_trd(h->dS, h->d_trd_grp, h->trd_chunks.data(), static_cast<int>(h->trd_chunks.size()),
                                   h->d_trd_bar, h->count, s0, s1, tmaps, h->max_n_trd, h->trd_bis_lanes, st,
                                   h->trd_marks);
@@ -872,6 +875,13 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_TRDBT: t = x.trd ? tiles_trd_bt(x.n) : 0; break;
         case TK_TRDOZP: t = x.trd ? tiles_trd_ozp(x.n) : 0; break;
         case TK_TRDOZG: t = x.trd ? tiles_trd_ozg(x.n) : 0; break;
+        case TK_BTPACK: t = x.trd ? tiles_bt_pack(x.n) : 0; break;
+        case TK_BTGRAM: t = x.trd ? tiles_bt_gram(x.n) : 0; break;
+        case TK_BTTFAC: t = x.trd ? tiles_bt_tfac(x.n) : 0; break;
+        case TK_BTROWS: t = x.trd ? tiles_bt_rows(x.n) : 0; break;
+        case TK_BTCOLS: t = x.trd ? tiles_bt_cols(x.n) : 0; break;
+        case TK_BTUPD: t = x.trd ? tiles_bt_update(x.n) : 0; break;
+        case TK_BTFIN: t = x.trd ? tiles_bt_final(x.n) : 0; break;
         case TK_JBBLK: t = x.trd ? 0 : tiles_jb_blocks(x.n); break;
         case TK_JBLOAD: t = x.trd ? 0 : tiles_jb_load(x.n); break;
         case TK_JBROWS: t = x.trd ? 0 : tiles_jb_rows(x.n); break;

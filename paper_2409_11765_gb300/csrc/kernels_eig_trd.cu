@@ -45,43 +45,9 @@
 #include <cmath>
 #include "device_common.cuh"
 #include "ozaki.cuh"
+#include "trd_common.cuh"
 
 namespace cmaes_gb300 {
-
-// --------------------------------------------------------------------------
-// Scratch of one search (Search::trd_v: TV_COUNT vectors of ldn doubles,
-// Search::trd_i: TI_COUNT vectors of ldn ints) and its matrices: W (the matrix
-// being reduced) = EA, reflectors = EX (column k holds v_k in rows k+1..),
-// eigenvectors of T = ET (column t), inverse-iteration factors = EA, EG, EH
-// (after the reduction), I - V^T V in FP32 = EG, the Newton-Schulz iterates
-// alternate between ET and EA and end in EA.
-// --------------------------------------------------------------------------
-enum { TV_D = 0, TV_E, TV_ES, TV_E2, TV_TAU, TV_LAMB, TV_LAMS, TV_P0, TV_P1, TV_SD, TV_SCAL };
-enum { TI_B0 = 0, TI_B1, TI_RANK, TI_CL0, TI_TFLAG };
-// scalars at TV_SCAL: ||T|| bound, pivmin, split threshold, cluster threshold,
-// and the orthogonality defect max |(I - V^T V) / 2| before each Newton-Schulz
-// step (as ordered bit patterns for atomicMax)
-constexpr double kTrdSplit = 4.0;
-constexpr double kTrdClus = 1e-13;
-constexpr int kTrdClusMax = 64;      // Gram-Schmidt chunk of a longer cluster
-constexpr int kTrdNsSteps = 3;
-constexpr double kTrdNsSkip = 5e-9;  // one step leaves 1.5 (2 * 5e-9)^2 < eps64
-// V^T V is formed only for 64 x 64 tiles holding a pair of vectors of one
-// block whose eigenvalues lie within kTrdNsBand ||T||: for a pair further apart
-// inverse iteration already leaves |v_i^T v_j| <~ eps64 / kTrdNsBand ~ 1e-14.
-constexpr double kTrdNsBand = 1e-2;
-constexpr double kTrdEps = 0x1p-53;
-constexpr long long kTrdWaitCycles = 2000000000LL;  // ~1 s at 2 GHz
-constexpr int kTrdNT = 256;
-
-__device__ __forceinline__ bool trd_due(const Search& s) { return s.trd && !s.done && s.eig_due; }
-
-__device__ __forceinline__ double* tv(const Search& s, int which) {
-  return s.trd_v + static_cast<long long>(which) * s.ldn;
-}
-__device__ __forceinline__ int* ti(const Search& s, int which) {
-  return s.trd_i + static_cast<long long>(which) * s.ldn;
-}
 
 __device__ __forceinline__ double warp_sum_xor(double v) {
 #pragma unroll
@@ -647,8 +613,8 @@ int tiles_trd_sq(int n) { const int T = ceil_div(n, kGBM); return T * T; }
 
 int tiles_trd_ozp(int n) { return oz_rows_padded(n) / 64; }
 int tiles_trd_ozg(int n) { return ceil_div(n, kOzBM) * ceil_div(n, kOzBN); }
-size_t trd_oz_bytes(int n) { return oz_bytes(n, n); }
-int trd_oz_exps(int n) { return 4 * oz_rows_padded(n); }
+size_t trd_oz_bytes(int n) { return trd_oz_layout(n).total; }
+int trd_oz_exps(int n) { return trd_oz_layout(n).etotal; }
 
 __device__ __forceinline__ bool trd_ns_skipped(const Search& s, int pass) {
   return pass > 0 && __ldcg(&tv(s, TV_SCAL)[3 + pass]) <= kTrdNsSkip;  // the previous step was enough
@@ -850,80 +816,15 @@ __global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass
 }
 
 // --------------------------------------------------------------------------
-// 6. Back-transformation B = Q V' (reflectors applied in reverse order to R
-// columns held in shared memory, one warp per column), canonical sign, and
-// the column order of ascending eigenvalues.
+// 6. Back-transformation B = Q V' of the smaller sizes (reflectors applied in
+// reverse order, one warp per column), canonical sign, and the column order of
+// ascending eigenvalues; kernels_eig_trd_bt.cu takes n >= kBtBlockedMinN.
 // --------------------------------------------------------------------------
-__host__ __device__ inline int trd_bt_cols(int n) { return n <= 3200 ? 8 : 6; }
-constexpr int kTrdBtRegMaxN = 2048;  // largest n whose columns fit in registers
-int tiles_trd_bt(int n) { return ceil_div(n, trd_bt_cols(n)); }
-size_t trd_bt_smem(int max_n) {
-  int best = 0;
-  for (int n = 1; n <= max_n; n += (n < 3200 ? 3199 : 1)) best = std::max(best, trd_bt_cols(n) * n);
-  best = std::max(best, trd_bt_cols(max_n) * max_n);
-  return static_cast<size_t>(best) * 8;
-}
+__host__ __device__ inline int trd_bt_cols(int n) { return 8; }
+int tiles_trd_bt(int n) { return trd_bt_blocked(n) ? 0 : ceil_div(n, trd_bt_cols(n)); }
 
-__global__ void __launch_bounds__(kTrdNT) k_trd_backtf(Search* S, TileMap tm) {
-  extern __shared__ double cols[];
-  int tile;
-  const int si = find_search(tm, tile);
-  Search& s = S[si];
-  if (!trd_due(s)) return;
-  const int n = s.n, R = trd_bt_cols(n);
-  if (n <= kTrdBtRegMaxN) return;  // k_trd_backtf_reg takes these sizes
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const long long L = s.ldn;
-  const int t0 = tile * R;
-  const int nc = min(R, n - t0);
-  const double* Vs = s.EA;
-  for (int c = 0; c < nc; ++c)
-    for (int i = threadIdx.x; i < n; i += kTrdNT) cols[c * n + i] = Vs[i + L * (t0 + c)];
-  __syncthreads();
-  if (warp < nc) {
-    double* x = cols + warp * n;
-    const double* tau = tv(s, TV_TAU);
-    const double* Hv = s.EX;
-    for (int k = n - 2; k >= 0; --k) {
-      const double tk = tau[k];
-      if (tk == 0.0) continue;
-      const double* v = Hv + L * k;
-      double p = 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) p = fma(v[i], x[i], p);
-      p = tk * warp_sum_xor(p);
-      for (int i = k + 1 + lane; i < n; i += 32) x[i] = fma(-p, v[i], x[i]);
-      __syncwarp();
-    }
-    // sign: the entry of largest magnitude (the first on ties) positive
-    double best = -1.0, val = 0.0;
-    int bi = 0x7fffffff;
-    for (int i = lane; i < n; i += 32) {
-      const double a = fabs(x[i]);
-      if (a > best) {
-        best = a;
-        val = x[i];
-        bi = i;
-      }
-    }
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) {
-      const double ob = __shfl_xor_sync(0xffffffffu, best, o);
-      const double ov = __shfl_xor_sync(0xffffffffu, val, o);
-      const int oi = __shfl_xor_sync(0xffffffffu, bi, o);
-      if (ob > best || (ob == best && oi < bi)) {
-        best = ob;
-        val = ov;
-        bi = oi;
-      }
-    }
-    const double sg = val < 0.0 ? -1.0 : 1.0;
-    double* Bc = s.B + L * ti(s, TI_RANK)[t0 + warp];
-    for (int i = lane; i < n; i += 32) Bc[i] = sg * x[i];
-  }
-}
-
-// The same for n <= 32 RMAX with each column held in registers (element
-// lane + 32 r in x[r]): the column never moves; each reflector is staged once
+// Each column held in registers (element lane + 32 r in x[r]; n <= 32 RMAX):
+// the column never moves; each reflector is staged once
 // per CTA in shared memory (double-buffered: the next one is loaded while the
 // current one is applied) and rows at or above its first row are skipped 256
 // at a time.
@@ -935,7 +836,7 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_backtf_reg(Search* S, TileMap tm
   Search& s = S[si];
   if (!trd_due(s)) return;
   const int n = s.n;
-  if (n > 32 * RMAX || (RMAX > 16 && n <= 16 * RMAX)) return;  // the other variants take these sizes
+  if (n > 32 * RMAX || trd_bt_blocked(n)) return;  // the blocked form takes these sizes
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int t = tile * trd_bt_cols(n) + warp;
   const bool active = warp < trd_bt_cols(n) && t < n;  // idle warps still join the barriers
@@ -1079,9 +980,8 @@ int trd_sytrd_blocks_per_sm(int max_n) {
 void trd_set_attributes(int max_n) {
   cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
                        static_cast<int>(trd_sytrd_smem(max_n)));
-  cudaFuncSetAttribute(k_trd_backtf, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(trd_bt_smem(max_n)));
   cudaFuncSetAttribute(k_trd_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
+  bt_set_attributes();
 }
 
 // marks (optional, kTrdStages + 1 events): recorded before the reduction and
@@ -1129,13 +1029,14 @@ int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks
     k_trd_ns<<<tm.tsq.total, kGNT, 0, st>>>(S, tm.tsq, pass);
   }
   mark(5);
-  k_trd_backtf_reg<16><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // n <= 512
-  k_trd_backtf_reg<32><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // 512 < n <= 1024
-  k_trd_backtf_reg<64><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);   // 1024 < n <= 2048
-  if (max_n > kTrdBtRegMaxN) k_trd_backtf<<<tm.tbt.total, kTrdNT, trd_bt_smem(max_n), st>>>(S, tm.tbt);
+  if (tm.tbt.total > 0) {  // n < kBtBlockedMinN
+    k_trd_backtf_reg<16><<<tm.tbt.total, kTrdNT, 0, st>>>(S, tm.tbt);
+    ++nl;
+  }
+  nl += launch_bt(S, tm, max_n, st);  // the larger ones
   k_trd_finish<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);
   mark(6);
-  return nl + 9 + 3 * kTrdNsSteps + (max_n > kTrdBtRegMaxN ? 1 : 0);
+  return nl + 6 + 3 * kTrdNsSteps;
 }
 
 }  // namespace cmaes_gb300

@@ -105,18 +105,19 @@ __device__ __forceinline__ int oz_off(int r, int k) {
 }
 
 // --------------------------------------------------------------------------
-// Packing of one 64-row block of an operand: x(r, k) = src[r * sr + k * sk]
-// for r < R, k < K (zero elsewhere), rows rb * 64 .. rb * 64 + 63, K chunks
-// 0 .. nks - 1. All kOzNT threads of the block call it; sh_e holds 64 ints.
-// Writes the row exponents to e_out[r] (r < padded rows).
+// Packing of one 64-row block of an operand: x(r, k) = get(r, k) for r < R,
+// k < K (zero elsewhere; get is called only inside), rows rb * 64 ..
+// rb * 64 + 63, K chunks 0 .. nks - 1. kfast: consecutive k are contiguous in
+// memory (then 4 threads read 32 consecutive k of a row), else consecutive
+// rows are (a warp reads 32 consecutive rows). All kOzNT threads of the block
+// call it; sh_e holds 64 ints. Writes the row exponents to e_out[r] (r < the
+// padded row count).
 // --------------------------------------------------------------------------
-__device__ __forceinline__ void oz_pack_block(const double* __restrict__ src, long long sr, long long sk, int R,
-                                              int K, int rb, int nks, unsigned char* __restrict__ out,
-                                              int* __restrict__ e_out, int* sh_e) {
+template <class Get>
+__device__ __forceinline__ void oz_pack_block_get(const Get& get, bool kfast, int R, int K, int rb, int nks,
+                                                  unsigned char* __restrict__ out, int* __restrict__ e_out,
+                                                  int* sh_e) {
   const int tid = threadIdx.x;
-  const bool kfast = (sk == 1);
-  // thread -> (row, K octet): K-contiguous sources read 32 consecutive K of a
-  // row per 4 threads, row-contiguous ones 32 consecutive rows per warp
   const int rl = kfast ? (tid >> 2) : (tid & 63);
   const int oc = kfast ? (tid & 3) : (tid >> 6);
   const int r = rb * 64 + rl;
@@ -124,26 +125,24 @@ __device__ __forceinline__ void oz_pack_block(const double* __restrict__ src, lo
   __syncthreads();
   int emax = kOzZeroExp;
   if (r < R) {
-    const double* row = src + static_cast<long long>(r) * sr;
     for (int k = oc * 8; k < K; k += 32) {
 #pragma unroll
       for (int u = 0; u < 8; ++u)
-        if (k + u < K) emax = max(emax, oz_exponent(row[static_cast<long long>(k + u) * sk]));
+        if (k + u < K) emax = max(emax, oz_exponent(get(r, k + u)));
     }
   }
   atomicMax(&sh_e[rl], emax);
   __syncthreads();
   const int e = sh_e[rl];
   if (oc == 0) e_out[r] = e;
-  const double* row = src + static_cast<long long>(r < R ? r : 0) * sr;
   unsigned char* base = out + static_cast<long long>(rb) * oz_pitch(nks);
   for (int kc = 0; kc < nks; ++kc) {
     uint32_t pk[kOzS][4];
 #pragma unroll
     for (int u = 0; u < 8; u += 2) {
       const int k = kc * kOzKS + oc * 8 + u;
-      const double x0 = (r < R && k < K) ? row[static_cast<long long>(k) * sk] : 0.0;
-      const double x1 = (r < R && k + 1 < K) ? row[static_cast<long long>(k + 1) * sk] : 0.0;
+      const double x0 = (r < R && k < K) ? get(r, k) : 0.0;
+      const double x1 = (r < R && k + 1 < K) ? get(r, k + 1) : 0.0;
       uint32_t d0[kOzS], d1[kOzS];
       oz_digits(x0, e, d0);
       oz_digits(x1, e, d1);
@@ -155,6 +154,28 @@ __device__ __forceinline__ void oz_pack_block(const double* __restrict__ src, lo
     for (int p = 0; p < kOzS; ++p)
       *reinterpret_cast<uint4*>(blk + p * kOzBlk) = make_uint4(pk[p][0], pk[p][1], pk[p][2], pk[p][3]);
   }
+}
+
+// The same for a strided view x(r, k) = src[r * sr + k * sk].
+__device__ __forceinline__ void oz_pack_block(const double* __restrict__ src, long long sr, long long sk, int R,
+                                              int K, int rb, int nks, unsigned char* __restrict__ out,
+                                              int* __restrict__ e_out, int* sh_e) {
+  oz_pack_block_get(
+      [=] __device__(int r, int k) { return src[static_cast<long long>(r) * sr + static_cast<long long>(k) * sk]; },
+      sk == 1, R, K, rb, nks, out, e_out, sh_e);
+}
+
+// 2^e as a double (0 or infinity outside the normal range).
+__device__ __forceinline__ double oz_pow2(int e) {
+  if (e >= -1022 && e <= 1023) return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
+  return ldexp(1.0, e);
+}
+
+// The FP64 value of an output element from its tile sums (oz_tile) and the
+// exponents of its row of A and its row of B.
+__device__ __forceinline__ double oz_value(long long W, float L, int ea, int eb) {
+  if (ea <= kOzZeroExp || eb <= kOzZeroExp) return 0.0;
+  return (static_cast<double>(W) + static_cast<double>(L)) * oz_pow2(ea + eb - 44);
 }
 
 // --------------------------------------------------------------------------
@@ -182,11 +203,6 @@ __device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
   }
 }
 
-// 2^e as a double (0 or infinity outside the normal range).
-__device__ __forceinline__ double oz_pow2(int e) {
-  if (e >= -1022 && e <= 1023) return __longlong_as_double(static_cast<long long>(e + 1023) << 52);
-  return ldexp(1.0, e);
-}
 
 // --------------------------------------------------------------------------
 // The tile: out(i, j) for rows i0 + 0..127 of A and columns j0 + 0..63 (rows
