@@ -313,7 +313,7 @@ static void enqueue_eig(cmaes_t h, int s0, int s1, cudaStream_t st) {
                         h->tiles(TK_TRDBT, s0, s1), h->tiles(TK_TRDOZP, s0, s1), h->tiles(TK_TRDOZG, s0, s1),
                         h->tiles(TK_BTPACK, s0, s1), h->tiles(TK_BTGRAM, s0, s1), h->tiles(TK_BTTFAC, s0, s1),
                         h->tiles(TK_BTROWS, s0, s1), h->tiles(TK_BTCOLS, s0, s1), h->tiles(TK_BTUPD, s0, s1),
-                        h->tiles(TK_BTFIN, s0, s1)};
+                        h->tiles(TK_BTFIN, s0, s1),  h->tiles(TK_TRDS2KP, s0, s1), h->tiles(TK_TRDS2K, s0, s1)};
     const int nl = launch_eig_trd(h->dS, h->d_trd_grp, h->trd_chunks.data(), static_cast<int>(h->trd_chunks.size()),
                                   h->d_trd_bar, h->count, s0, s1, tmaps, h->max_n_trd, h->trd_bis_lanes, st,
                                   h->trd_marks);
@@ -793,7 +793,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     CREATE_TRY(cudaGetDevice(&dev));
     CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     trd_set_attributes(h->max_n_trd);
-    const int per_sm = trd_sytrd_blocks_per_sm(h->max_n_trd);
+    const int per_sm = trd_reduce_blocks_per_sm(h->max_n_trd);
     long long budget = static_cast<long long>(per_sm) * sms;
     double wsum = 0.0;
     int ntrd = 0;
@@ -882,6 +882,8 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         case TK_BTCOLS: t = x.trd ? tiles_bt_cols(x.n) : 0; break;
         case TK_BTUPD: t = x.trd ? tiles_bt_update(x.n) : 0; break;
         case TK_BTFIN: t = x.trd ? tiles_bt_final(x.n) : 0; break;
+        case TK_TRDS2KP: t = x.trd ? tiles_trd_s2k_pack(x.n) : 0; break;
+        case TK_TRDS2K: t = x.trd ? tiles_trd_s2k(x.n) : 0; break;
         case TK_JBBLK: t = x.trd ? 0 : tiles_jb_blocks(x.n); break;
         case TK_JBLOAD: t = x.trd ? 0 : tiles_jb_load(x.n); break;
         case TK_JBROWS: t = x.trd ? 0 : tiles_jb_rows(x.n); break;

@@ -120,7 +120,7 @@ int tiles_square(int n);                    // all 64 x 64 tiles of n x n
 
 enum TileKind {
   TK_SAMPLE_Z = 0, TK_PANEL, TK_COLRED, TK_RANK, TK_ROWS, TK_RECOMB, TK_GEMV, TK_SYM, TK_SQUARE,
-  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG, TK_BTPACK, TK_BTGRAM, TK_BTTFAC, TK_BTROWS, TK_BTCOLS, TK_BTUPD, TK_BTFIN, TK_COUNT
+  TK_COVP, TK_RANK2D, TK_TCSAMPLE, TK_TCOBJ, TK_TCCOVP, TK_TCSYM, TK_FLAT, TK_FLATSYM, TK_REEVAL, TK_JBBLK, TK_JBLOAD, TK_JBROWS, TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG, TK_BTPACK, TK_BTGRAM, TK_BTTFAC, TK_BTROWS, TK_BTCOLS, TK_BTUPD, TK_BTFIN, TK_TRDS2KP, TK_TRDS2K, TK_COUNT
 };
 
 // launchers (kernels_gen.cu)
@@ -237,13 +237,16 @@ int tiles_bt_cols(int n);    // 64-column tiles of a 128 x n product
 int tiles_bt_update(int n);  // 128 x 64 tiles of the largest panel's update
 int tiles_bt_final(int n);   // 8 columns per tile
 void bt_set_attributes();
-size_t trd_sytrd_smem(int max_n);
-int trd_sytrd_blocks_per_sm(int max_n);
+size_t trd_reduce_smem(int max_n);
+int trd_reduce_blocks_per_sm(int max_n);
+int tiles_trd_s2k_pack(int n);  // 64-row blocks of the reduction's trailing-update operands
+int tiles_trd_s2k(int n);       // 128 x 64 tiles of its trailing update
 void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
 struct TrdMaps {
   TileMap tt, tbis, tsq, tbt, ozp, ozg;  // TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG
   TileMap btpack, btgram, bttfac, btrows, btcols, btupd, btfin;  // TK_BTPACK .. TK_BTFIN
+  TileMap s2kp, s2k;  // TK_TRDS2KP, TK_TRDS2K
 };
 int launch_bt(Search* S, const TrdMaps& m, int max_n, cudaStream_t st);
 int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,

@@ -86,89 +86,212 @@ __device__ bool trd_group_sync(unsigned* ctr, unsigned target, int* err, int* sh
 }
 
 // --------------------------------------------------------------------------
-// 1. Householder tridiagonalisation. CTA blockIdx.x works for search
-// grp[b].x as member grp[b].y of a group of grp[b].z CTAs; column j of the
-// trailing matrix belongs to member j mod G, and within it to warp
-// (j div G) mod 8. Dynamic shared memory: v and w of the previous step and v
-// of the current one (3 n doubles).
+// 1. Householder tridiagonalisation in panels of kPnb columns (the blocked
+// form of LAPACK's dsytrd / dlatrd). Within panel [k0, k1) the matrix A (EA)
+// is only read: the current matrix is A - V W^T - W V^T with V the panel's
+// reflectors so far (columns k0.. of EX) and W (columns 0.. of EG) built step
+// by step; after the panel the trailing part of A takes that rank-2 kPnb
+// update as one FP64-accurate product on the tensor cores (k_trd_s2k_*).
+// CTA blockIdx.x works for search grp[b].x as member r = grp[b].y of a group
+// of G = grp[b].z CTAs: it owns the columns j with j mod G = r (the
+// symmetric product) and the 32-row chunks c with c mod G = r (the corrected
+// column and its partial sums). Step k (panel column j = k - k0):
+//   A. w of step k - 1 on the own rows; column k of the current matrix,
+//      c = A(:, k) - V W(k, :)^T - W V(k, :)^T, on the own rows below the
+//      diagonal (to cbuf); partial sums of |c(k+2:)|^2, W^T c(k+2:) and
+//      V^T c(k+2:);                                              group barrier
+//   B. (every CTA) the reflector of c from the summed partials, its vector v,
+//      u_W = W^T v and u_V = V^T v; on the own columns
+//      p(j') = tau (A(:, j')^T v - V(j', :) u_W - W(j', :) u_V), and the
+//      partial p . v;                                             group barrier
+// and w = p - (tau / 2)(p . v) v completes at the next step's A. Barrier m
+// (1-based, counted over the whole reduction) waits for G m arrivals: the
+// one after the symmetrisation is m = 1, step k's are 2k + 2 and 2k + 3.
+// Dynamic shared memory: v (n doubles).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTrdNT) k_trd_sytrd(Search* S, const int4* grp) {
-  extern __shared__ double tsm[];
+__global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp, int q) {
+  extern __shared__ double vsm[];
+  __shared__ double sVk[kPnb], sWk[kPnb], su[2 * kPnb];
   __shared__ double red[kTrdNT / 32 + 8];
   __shared__ int sh_ok;
   const int4 g = grp[blockIdx.x];
   Search& s = S[g.x];
   if (!trd_due(s)) return;
-  const int n = s.n;
+  const int n = s.n, k0 = kPnb * q;
+  if (k0 >= n) return;
+  const int k1 = min(k0 + kPnb, n);
   const long long L = s.ldn;
   const int r = g.y, G = g.z;
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   constexpr int NW = kTrdNT / 32;
-  double* W = s.EA;
+  double* A = s.EA;
   double* Hv = s.EX;
-  const double* C = s.C;
+  double* Wp = s.EG;
   double* d = tv(s, TV_D);
   double* e = tv(s, TV_E);
   double* tau = tv(s, TV_TAU);
-  double* pbuf = tv(s, TV_P0);  // two buffers: step k uses pbuf + (k & 1) L
-  double* sdot = tv(s, TV_SD);  // per-CTA partial p.v, two buffers of L / 2
+  double* cbuf = tv(s, TV_P0);
+  double* pbuf = tv(s, TV_P1);
+  double* pvp = tv(s, TV_SD);  // per-CTA p . v
+  double* part = s.EH;         // per-CTA partial sums, kPartStride apart
   unsigned* bar = s.trd_bar;
-  double* vprev = tsm;
-  double* wprev = tsm + n;
-  double* vcur = tsm + 2 * n;
-  // W = (C + C^T) / 2, owned columns only
-  for (int j = r; j < n; j += G)
-    for (int i = tid; i < n; i += kTrdNT) W[i + L * j] = 0.5 * (C[i + L * j] + C[j + L * i]);
-  for (int i = tid; i < n; i += kTrdNT) {
-    vprev[i] = 0.0;
-    wprev[i] = 0.0;
-  }
-  unsigned nb = 0;
-  if (G > 1) {
-    if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
-  } else {
+  auto barrier = [&](unsigned m) -> bool {
+    if (G > 1) return trd_group_sync(bar, static_cast<unsigned>(G) * m, s.err, &sh_ok);
     __syncthreads();
+    return true;
+  };
+  if (q == 0) {  // A = (C + C^T) / 2, owned columns
+    const double* C = s.C;
+    for (int jc = r; jc < n; jc += G)
+      for (int i = tid; i < n; i += kTrdNT) A[i + L * jc] = 0.5 * (C[i + L * jc] + C[jc + L * i]);
+    if (!barrier(1u)) return;
   }
-  for (int k = 0; k + 1 < n; ++k) {
-    // column k with the pending update of step k - 1
-    for (int i = k + tid; i < n; i += kTrdNT)
-      vcur[i] = fma(-wprev[i], vprev[k], fma(-vprev[i], wprev[k], __ldcg(&W[i + L * k])));
-    __syncthreads();
-    // its reflector (warp 0, fixed-order sum)
+  // the first own 32-row chunk at or after row `row`
+  auto first_chunk = [&](int row) {
+    const int c0 = row >> 5;
+    return c0 + ((r - c0 % G) % G + G) % G;
+  };
+  // w of step k - 1 (panel column j - 1) on the own rows i >= k
+  auto finish_w = [&](int k, int j, double tprev) {
     if (warp == 0) {
-      double part = 0.0;
-      for (int i = k + 2 + lane; i < n; i += 32) part = fma(vcur[i], vcur[i], part);
-      const double xn2 = warp_sum_xor(part);
-      if (lane == 0) {
-        const double alpha = vcur[k + 1];
-        double t = 0.0, beta = alpha, scale = 0.0;
-        if (xn2 > 0.0) {
-          beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
-          t = (beta - alpha) / beta;
-          scale = 1.0 / (alpha - beta);
-        }
-        red[NW] = t;
-        red[NW + 1] = beta;
-        red[NW + 2] = scale;
-        red[NW + 3] = vcur[k];
-      }
+      double sp = 0.0;
+      for (int c = lane; c < G; c += 32) sp += __ldcg(&pvp[c]);
+      sp = warp_sum_xor(sp);
+      if (lane == 0) red[NW] = 0.5 * tprev * sp;
     }
     __syncthreads();
-    const double t = red[NW], scale = red[NW + 2];
-    for (int i = k + 2 + tid; i < n; i += kTrdNT) vcur[i] *= scale;
-    if (tid == 0) vcur[k + 1] = 1.0;
-    __syncthreads();
-    if (r == 0) {
-      for (int i = k + 1 + tid; i < n; i += kTrdNT) Hv[i + L * k] = vcur[i];
+    const double half = red[NW];
+    for (int c = first_chunk(k) + G * warp; 32 * c < n; c += G * NW) {
+      const int i = 32 * c + lane;
+      if (i >= k && i < n) Wp[i + L * (j - 1)] = fma(-half, vsm[i], __ldcg(&pbuf[i]));
+    }
+    return half;
+  };
+  double tprev = 0.0;
+  for (int k = k0; k < k1; ++k) {
+    const int j = k - k0;
+    // ---------------- A ----------------
+    if (j > 0) {
+      const double half = finish_w(k, j, tprev);
       if (tid == 0) {
-        d[k] = red[NW + 3];
-        e[k] = red[NW + 1];
+        sVk[j - 1] = 1.0;                                // v_{k-1}(k)
+        sWk[j - 1] = fma(-half, 1.0, __ldcg(&pbuf[k]));  // w_{k-1}(k)
+      }
+    }
+    for (int l = tid; l + 1 < j; l += kTrdNT) {  // row k of the older columns
+      sVk[l] = __ldcg(&Hv[k + L * (k0 + l)]);
+      sWk[l] = __ldcg(&Wp[k + L * l]);
+    }
+    __syncthreads();
+    if (k == n - 1) {  // the last diagonal entry
+      if (r == 0 && tid == 0) {
+        double acc = __ldcg(&A[k + L * k]);
+        for (int l = 0; l < j; ++l) acc = fma(-2.0 * sVk[l], sWk[l], acc);
+        d[k] = acc;
+      }
+      return;
+    }
+    double nrm = 0.0;
+    for (int c = first_chunk(k + 1) + G * warp; 32 * c < n; c += G * NW) {
+      const int i = 32 * c + lane;
+      if (i > k && i < n) {
+        double ci = __ldcg(&A[i + L * k]);
+        int l = 0;
+        for (; l + 8 <= j; l += 8) {  // eight columns' loads in flight
+          double hv[8], wv[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) {
+            hv[u] = __ldcg(&Hv[i + L * (k0 + l + u)]);
+            wv[u] = __ldcg(&Wp[i + L * (l + u)]);
+          }
+#pragma unroll
+          for (int u = 0; u < 8; ++u) ci = fma(-hv[u], sWk[l + u], fma(-wv[u], sVk[l + u], ci));
+        }
+        for (; l < j; ++l)
+          ci = fma(-__ldcg(&Hv[i + L * (k0 + l)]), sWk[l], fma(-__ldcg(&Wp[i + L * l]), sVk[l], ci));
+        vsm[i] = ci;
+        cbuf[i] = ci;
+        if (i >= k + 2) nrm = fma(ci, ci, nrm);
+      }
+    }
+    nrm = warp_sum_xor(nrm);
+    if (lane == 0) red[warp] = nrm;
+    __syncthreads();
+    double* pr = part + static_cast<long long>(r) * kPartStride;
+    if (tid == 0) {
+      double a = 0.0;
+      for (int w = 0; w < NW; ++w) a += red[w];
+      pr[0] = a;
+    }
+    // W^T c and V^T c over the own rows i >= k + 2 (one warp per column)
+    for (int l = warp; l < 2 * j; l += NW) {
+      const double* col = l < j ? Wp + L * l : Hv + L * (k0 + l - j);
+      double acc = 0.0;
+      for (int c = first_chunk(k + 2); 32 * c < n; c += G) {
+        const int i = 32 * c + lane;
+        if (i >= k + 2 && i < n) acc = fma(__ldcg(&col[i]), vsm[i], acc);
+      }
+      acc = warp_sum_xor(acc);
+      if (lane == 0) pr[1 + l] = acc;
+    }
+    if (!barrier(2u * k + 2u)) return;
+    // ---------------- B ----------------
+    if (warp == 0) {
+      double a = 0.0;
+      for (int c = lane; c < G; c += 32) a += __ldcg(&part[static_cast<long long>(c) * kPartStride]);
+      a = warp_sum_xor(a);
+      if (lane == 0) red[NW + 1] = a;
+    }
+    for (int l = tid; l < 2 * j; l += kTrdNT) {
+      const double* pp = part + 1 + l;
+      double a = 0.0;
+      int c = 0;
+      for (; c + 8 <= G; c += 8) {  // the same order, eight loads in flight
+        double x[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) x[u] = __ldcg(&pp[static_cast<long long>(c + u) * kPartStride]);
+#pragma unroll
+        for (int u = 0; u < 8; ++u) a += x[u];
+      }
+      for (; c < G; ++c) a += __ldcg(&pp[static_cast<long long>(c) * kPartStride]);
+      su[l] = a;
+    }
+    if (tid == 32) {  // the diagonal entry of column k
+      double acc = __ldcg(&A[k + L * k]);
+      for (int l = 0; l < j; ++l) acc = fma(-2.0 * sVk[l], sWk[l], acc);
+      red[NW + 2] = acc;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      const double xn2 = red[NW + 1];
+      const double alpha = __ldcg(&cbuf[k + 1]);
+      double t = 0.0, beta = alpha, scale = 0.0;
+      if (xn2 > 0.0) {
+        beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+        t = (beta - alpha) / beta;
+        scale = 1.0 / (alpha - beta);
+      }
+      red[NW] = t;
+      red[NW + 3] = scale;
+      if (r == 0) {
+        d[k] = red[NW + 2];
+        e[k] = beta;
         tau[k] = t;
       }
     }
-    // owned columns j >= k + 1, two per warp at a time: pending update, then
-    // p_j = tau (A v)_j, and this CTA's share of p . v
-    double* pk = pbuf + (k & 1) * L;
+    __syncthreads();
+    const double t = red[NW], scale = red[NW + 3];
+    for (int i = k + 1 + tid; i < n; i += kTrdNT) vsm[i] = (i == k + 1) ? 1.0 : __ldcg(&cbuf[i]) * scale;
+    for (int l = tid; l < j; l += kTrdNT) {
+      su[l] = fma(scale, su[l], __ldcg(&Wp[(k + 1) + L * l]));                  // u_W
+      su[j + l] = fma(scale, su[j + l], __ldcg(&Hv[(k + 1) + L * (k0 + l)]));  // u_V
+    }
+    __syncthreads();
+    for (int c = first_chunk(k + 1) + G * warp; 32 * c < n; c += G * NW) {
+      const int i = 32 * c + lane;
+      if (i > k && i < n) Hv[i + L * k] = vsm[i];
+    }
+    // own columns j' >= k + 1, two per warp at a time
     const int m0 = (k + 1 > r) ? (k + 1 - r + G - 1) / G : 0;
     double pv = 0.0;
     for (int m = m0 + warp;; m += 2 * NW) {
@@ -176,88 +299,128 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_sytrd(Search* S, const int4* grp
       if (j1 >= n) break;
       const bool two = j2 < n;
       const int j2c = two ? j2 : j1;
-      const double vp1 = vprev[j1], wp1 = wprev[j1], vp2 = vprev[j2c], wp2 = wprev[j2c];
+      const double* A1 = A + L * j1;
+      const double* A2 = A + L * j2c;
       double q1 = 0.0, q2 = 0.0;
-      double* W1 = W + L * j1;
-      double* W2 = W + L * j2c;
       int i = k + 1 + lane;
-      // four rows per lane in flight: the column loads are issued before use
       for (; i + 96 < n; i += 128) {
         double a1[4], a2[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          a1[u] = W1[i + 32 * u];
-          a2[u] = two ? W2[i + 32 * u] : 0.0;
+          a1[u] = A1[i + 32 * u];
+          a2[u] = two ? A2[i + 32 * u] : 0.0;
         }
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
-          const int ii = i + 32 * u;
-          const double vi = vprev[ii], wi = wprev[ii], ci = vcur[ii];
-          a1[u] = fma(-wi, vp1, fma(-vi, wp1, a1[u]));
-          q1 = fma(a1[u], ci, q1);
-          if (two) {
-            a2[u] = fma(-wi, vp2, fma(-vi, wp2, a2[u]));
-            q2 = fma(a2[u], ci, q2);
-          }
-        }
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          W1[i + 32 * u] = a1[u];
-          if (two) W2[i + 32 * u] = a2[u];
+          const double vi = vsm[i + 32 * u];
+          q1 = fma(a1[u], vi, q1);
+          q2 = fma(a2[u], vi, q2);
         }
       }
       for (; i < n; i += 32) {
-        const double vi = vprev[i], wi = wprev[i], ci = vcur[i];
-        const double a1 = fma(-wi, vp1, fma(-vi, wp1, W1[i]));
-        W1[i] = a1;
-        q1 = fma(a1, ci, q1);
-        if (two) {
-          const double a2 = fma(-wi, vp2, fma(-vi, wp2, W2[i]));
-          W2[i] = a2;
-          q2 = fma(a2, ci, q2);
-        }
-        if (k == n - 2) d[n - 1] = a1;  // the last diagonal entry (i = j = n - 1)
+        const double vi = vsm[i];
+        q1 = fma(A1[i], vi, q1);
+        if (two) q2 = fma(A2[i], vi, q2);
+      }
+      for (int l = lane; l < j; l += 32) {
+        q1 = fma(-__ldcg(&Hv[j1 + L * (k0 + l)]), su[l], fma(-__ldcg(&Wp[j1 + L * l]), su[j + l], q1));
+        if (two)
+          q2 = fma(-__ldcg(&Hv[j2 + L * (k0 + l)]), su[l], fma(-__ldcg(&Wp[j2 + L * l]), su[j + l], q2));
       }
       q1 = t * warp_sum_xor(q1);
       q2 = t * warp_sum_xor(q2);
       if (lane == 0) {
-        pk[j1] = q1;
-        pv = fma(q1, vcur[j1], pv);
+        pbuf[j1] = q1;
+        pv = fma(q1, vsm[j1], pv);
         if (two) {
-          pk[j2] = q2;
-          pv = fma(q2, vcur[j2], pv);
+          pbuf[j2] = q2;
+          pv = fma(q2, vsm[j2], pv);
         }
       }
     }
     if (lane == 0) red[warp] = pv;
     __syncthreads();
-    double* sdk = sdot + (k & 1) * (L / 2);
     if (tid == 0) {
       double sp = 0.0;
       for (int w = 0; w < NW; ++w) sp += red[w];
-      sdk[r] = sp;
+      pvp[r] = sp;
     }
-    if (G > 1) {
-      if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
-    } else {
-      __syncthreads();
-    }
-    // w = p - (tau / 2) (p . v) v, kept with v for the next step's update
-    if (warp == 0) {
-      double sp = 0.0;
-      for (int c = lane; c < G; c += 32) sp += __ldcg(&sdk[c]);
-      sp = warp_sum_xor(sp);
-      if (lane == 0) red[NW + 4] = 0.5 * t * sp;
-    }
-    for (int i = k + 1 + tid; i < n; i += kTrdNT) wprev[i] = __ldcg(&pk[i]);
-    __syncthreads();
-    const double half = red[NW + 4];
-    for (int i = k + 1 + tid; i < n; i += kTrdNT) {
-      wprev[i] = fma(-half, vcur[i], wprev[i]);
-      vprev[i] = vcur[i];
-    }
-    __syncthreads();
+    if (!barrier(2u * k + 3u)) return;
+    tprev = t;
   }
+  // the panel's last w (its last step was a full one: k1 < n)
+  finish_w(k1, k1 - k0, tprev);
+}
+
+// The trailing update after panel q: A(k1:, k1:) -= V W^T + W V^T (rows and
+// columns k1.., K = kPnb) on the tensor cores, as two FP64-accurate products
+// whose operand rows are each all reflector entries or all W entries (one
+// exponent per row then fits both, whatever the scale of C). Pack tiles: the
+// 64-row blocks of V (first half of the tile range, sized for q = 0), then
+// those of W.
+int tiles_trd_s2k_pack(int n) { return n > kPnb ? 2 * (oz_rows_padded(n - kPnb) / 64) : 0; }
+int tiles_trd_s2k(int n) { return n > kPnb ? ceil_div(n - kPnb, kOzBM) * ceil_div(n - kPnb, kOzBN) : 0; }
+
+__global__ void __launch_bounds__(kOzNT) k_trd_s2k_pack(Search* S, TileMap tm, int q) {
+  __shared__ int sh_e[64];
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n, k0 = kPnb * q, k1 = k0 + kPnb;
+  if (k1 >= n) return;
+  const int R = n - k1, half = oz_rows_padded(n - kPnb) / 64;
+  const int which = tile >= half ? 1 : 0, rb = tile - which * half;
+  if (rb >= oz_rows_padded(R) / 64) return;
+  const TrdOz lay = trd_oz_layout(n);
+  const long long L = s.ldn;
+  const double* X = which == 0 ? s.EX + (k1 + L * k0) : s.EG + k1;  // V(k1 + i, l) or W(k1 + i, l)
+  oz_pack_block_get([=] __device__(int i, int l) { return X[i + L * l]; }, false, R, kPnb, rb, oz_nks(kPnb),
+                    s.ozp + (which == 0 ? lay.s2a : lay.s2b), s.oze + (which == 0 ? lay.ev : lay.ew), sh_e);
+}
+
+__global__ void __launch_bounds__(kOzNT, 1) k_trd_s2k(Search* S, TileMap tm, int q) {
+  extern __shared__ unsigned char dyn[];
+  __shared__ uint64_t bar[5];
+  __shared__ uint32_t tslot;
+  int tile;
+  const int si = find_search(tm, tile);
+  const Search& s = S[si];
+  if (!trd_due(s)) return;
+  const int n = s.n, k1 = kPnb * q + kPnb;
+  if (k1 >= n) return;
+  const int R = n - k1, TN = ceil_div(n - kPnb, kOzBN), mt = tile / TN, nt = tile % TN;
+  if (mt * kOzBM >= R || nt * kOzBN >= R) return;
+  const TrdOz lay = trd_oz_layout(n);
+  const unsigned char* Vp = s.ozp + lay.s2a;
+  const unsigned char* Wq8 = s.ozp + lay.s2b;
+  const int* ev = s.oze + lay.ev;
+  const int* ew = s.oze + lay.ew;
+  OzCtx cx;
+  oz_begin(cx, dyn, bar, &tslot);
+  long long Wq[32];
+  float Lq[32];
+  const long long pitch = oz_pitch(oz_nks(kPnb));
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int i = kOzBM * mt + 32 * (warp & 3) + lane, jb = kOzBN * nt + 32 * (warp >> 2);
+  const long long L = s.ldn;
+  double* Ai = s.EA + (k1 + i);
+  bool ok = true;
+  for (int part = 0; part < 2 && ok; ++part) {
+    // part 0: V_i . W_j, part 1: W_i . V_j
+    ok = oz_tile(cx, part == 0 ? Vp : Wq8, pitch, 2 * mt, part == 0 ? Wq8 : Vp, pitch, nt, oz_nks(kPnb), Wq, Lq);
+    if (ok && i < R) {
+      const int ei = part == 0 ? ev[i] : ew[i];
+      const int* eb = part == 0 ? ew : ev;
+#pragma unroll
+      for (int qq = 0; qq < 32; ++qq) {
+        const int jj = jb + qq;
+        if (jj < R) Ai[L * (k1 + jj)] -= oz_value(Wq[qq], Lq[qq], ei, eb[jj]);
+      }
+    }
+  }
+  if (!ok && threadIdx.x == 0) atomicOr(s.err, kDevErrTimeout);
+  oz_end(cx);
 }
 
 // --------------------------------------------------------------------------
@@ -964,13 +1127,13 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_finish(Search* S, int s0) {
 // --------------------------------------------------------------------------
 // Host side
 // --------------------------------------------------------------------------
-size_t trd_sytrd_smem(int max_n) { return static_cast<size_t>(3) * max_n * 8; }
+size_t trd_reduce_smem(int max_n) { return static_cast<size_t>(max_n) * 8; }
 
-int trd_sytrd_blocks_per_sm(int max_n) {
+int trd_reduce_blocks_per_sm(int max_n) {
   int b = 0;
-  const size_t smem = trd_sytrd_smem(max_n);
-  cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trd_sytrd, kTrdNT, smem) != cudaSuccess) {
+  const size_t smem = trd_reduce_smem(max_n);
+  cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trd_panel, kTrdNT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -978,8 +1141,9 @@ int trd_sytrd_blocks_per_sm(int max_n) {
 }
 
 void trd_set_attributes(int max_n) {
-  cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(trd_sytrd_smem(max_n)));
+  cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(trd_reduce_smem(max_n)));
+  cudaFuncSetAttribute(k_trd_s2k, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   cudaFuncSetAttribute(k_trd_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   bt_set_attributes();
 }
@@ -998,20 +1162,28 @@ int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks
   };
   mark(0);
   cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count, st);
-  for (int c = 0; c < nchunks; ++c) {
-    if (chunks[c].second <= 0) continue;
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(chunks[c].second);
-    cfg.blockDim = dim3(kTrdNT);
-    cfg.dynamicSmemBytes = trd_sytrd_smem(max_n);
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    attr[0].id = cudaLaunchAttributeCooperative;
-    attr[0].val.cooperative = 1;
-    cfg.attrs = attr;
-    cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_trd_sytrd, S, grp + chunks[c].first);
-    ++nl;
+  const int panels = ceil_div(max_n, kPnb);
+  for (int q = 0; q < panels; ++q) {
+    for (int c = 0; c < nchunks; ++c) {
+      if (chunks[c].second <= 0) continue;
+      cudaLaunchConfig_t cfg = {};
+      cfg.gridDim = dim3(chunks[c].second);
+      cfg.blockDim = dim3(kTrdNT);
+      cfg.dynamicSmemBytes = trd_reduce_smem(max_n);
+      cfg.stream = st;
+      cudaLaunchAttribute attr[1];
+      attr[0].id = cudaLaunchAttributeCooperative;
+      attr[0].val.cooperative = 1;
+      cfg.attrs = attr;
+      cfg.numAttrs = 1;
+      cudaLaunchKernelEx(&cfg, k_trd_panel, S, grp + chunks[c].first, q);
+      ++nl;
+    }
+    if (q + 1 < panels && tm.s2kp.total > 0 && tm.s2k.total > 0) {
+      k_trd_s2k_pack<<<tm.s2kp.total, kOzNT, 0, st>>>(S, tm.s2kp, q);
+      k_trd_s2k<<<tm.s2k.total, kOzNT, kOzSmem, st>>>(S, tm.s2k, q);
+      nl += 2;
+    }
   }
   mark(1);
   k_trd_blocks<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);

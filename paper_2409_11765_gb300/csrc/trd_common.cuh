@@ -54,11 +54,14 @@ __device__ __forceinline__ int* ti(const Search& s, int which) {
 //   w   the columns of W = Y_p^T V (or T_p W) as a packed operand (K = 128)
 //   g, tf  per panel, Y_p^T Y_p and T_p in FP64 (128 x 128, column-major)
 //   wf  W in FP64 (128 x n, column-major)
+//   s2a, s2b  the reduction's trailing update: [V W] and [W V] (K = 2 kPnb)
 // Search::oze, int offsets: v [0, np), w [np, 2 np), yt 2 np + 128 p,
 // y 2 np + 128 P + (padded rows of the earlier panels), t after y (128 per
 // panel), with np the padded n.
 // --------------------------------------------------------------------------
-constexpr int kBtNb = 128;  // reflectors per panel
+constexpr int kBtNb = 128;  // reflectors per panel of the back-transformation
+constexpr int kPnb = 64;    // columns per panel of the reduction
+constexpr int kPartStride = 2 * kPnb + 8;  // per-CTA partial sums of a reduction step
 // Back-transformation: blocked on the tensor cores above this size, one
 // register-resident column per warp in FP64 at and below it (where the
 // blocked form's fixed cost of six launches per panel dominates).
@@ -74,7 +77,7 @@ __host__ __device__ inline int trd_panel_nb(int n, int p) {
 }
 
 struct TrdOz {
-  size_t v, yt, y, t, w, g, tf, wf, total;  // bytes
+  size_t v, yt, y, t, w, g, tf, wf, s2a, s2b, total;  // bytes
   int ev, ew, eyt, ey, et, etotal;         // ints
 };
 
@@ -98,6 +101,10 @@ __host__ __device__ inline TrdOz trd_oz_layout(int n) {
   o += static_cast<size_t>(P) * kBtNb * kBtNb * 8;
   L.wf = o;
   o += trd_align256(static_cast<size_t>(kBtNb) * n * 8);
+  L.s2a = o;
+  o += trd_align256(oz_bytes(n, 2 * kPnb));
+  L.s2b = o;
+  o += trd_align256(oz_bytes(n, 2 * kPnb));
   L.total = o;
   int e = 0;
   L.ev = e;
