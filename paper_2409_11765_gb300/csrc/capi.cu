@@ -58,7 +58,7 @@ struct cmaes_s {
   int trd_bis_lanes = 8;  // lanes per eigenvalue of the multisection (1 for large batches)
   int4* d_trd_grp = nullptr;
   int trd_grp_blocks = 0;
-  std::vector<std::pair<int, int>> trd_chunks;  // (first CTA, CTAs) of each cooperative launch
+  std::vector<TrdChunk> trd_chunks;  // the cooperative launches of the reduction, panel by panel
   // per-stage times of the tridiagonal route in profiling mode: one set of
   // kTrdStages + 1 events per profiled generation, drained with the phases
   std::vector<cudaEvent_t> trd_pool;
@@ -786,48 +786,54 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     CREATE_TRY(cudaMemsetAsync(h->d_trd_bar, 0, sizeof(unsigned) * count, h->stream));
     for (int s = 0; s < count; ++s)
       if (h->hs[s].trd) h->hs[s].trd_bar = h->d_trd_bar + s;
-    // groups of the cooperative reduction: every tridiagonal-route search gets
-    // CTAs in proportion to n^3 (at least one, at most n / 16), within what
-    // can be resident at once
+    // groups of the cooperative reduction, within what can be resident at once
     int dev = 0, sms = 0;
     CREATE_TRY(cudaGetDevice(&dev));
     CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     trd_set_attributes(h->max_n_trd);
     const int per_sm = trd_reduce_blocks_per_sm(h->max_n_trd);
     long long budget = static_cast<long long>(per_sm) * sms;
-    double wsum = 0.0;
-    int ntrd = 0;
-    for (int s = 0; s < count; ++s)
-      if (h->hs[s].trd) {
-        wsum += std::pow(static_cast<double>(h->hs[s].n), 3.0);
-        ++ntrd;
-      }
     if (budget < 1) {
       set_error(h, CMAES_EUNSUPPORTED, "the tridiagonal reduction cannot be resident on this device");
       return fail(CMAES_EUNSUPPORTED);
     }
-    // groups in search order, cut into launches of at most `budget` CTAs that
-    // never split a group (more searches than resident CTAs: one CTA each,
-    // several launches)
-    const long long spare = budget > ntrd ? budget - ntrd : 0;
+    // one group table per panel of kTrdPanel columns: the searches with
+    // columns left in panel q share the resident CTAs in proportion to their
+    // trailing work (n - kTrdPanel q)^2, each with at least one CTA and at most
+    // (n - kTrdPanel q) / 16 and (n - kTrdPanel q)^2 / 16384 (enough work per
+    // step to outweigh the group barriers); launches of at most `budget` CTAs
+    // never split a group
     std::vector<int4> grp;
     h->trd_chunks.clear();
-    int chunk_start = 0;
-    for (int s = 0; s < count; ++s) {
-      const Search& x = h->hs[s];
-      if (!x.trd) continue;
-      const double share = std::pow(static_cast<double>(x.n), 3.0) / wsum;
-      int G = static_cast<int>(std::floor(share * static_cast<double>(spare))) + 1;
-      // at least 16 columns per CTA, and enough work per step to outweigh
-      // the group barrier (n^2 / 16384: one CTA below n = 181)
-      G = std::min(G, std::max(1, std::min(x.n / 16, static_cast<int>(static_cast<long long>(x.n) * x.n / 16384))));
-      if (static_cast<long long>(grp.size()) + G - chunk_start > budget) {
-        h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
-        chunk_start = static_cast<int>(grp.size());
+    const int panels = ceil_div(h->max_n_trd, kTrdPanel);
+    for (int q = 0; q < panels; ++q) {
+      double wsum = 0.0;
+      int nact = 0;
+      for (int s = 0; s < count; ++s) {
+        const Search& x = h->hs[s];
+        if (!x.trd || x.n <= kTrdPanel * q) continue;
+        const double m = static_cast<double>(x.n - kTrdPanel * q);
+        wsum += m * m;
+        ++nact;
       }
-      for (int r = 0; r < G; ++r) grp.push_back(make_int4(s, r, G, 0));
+      if (nact == 0) continue;
+      const long long spare = budget > nact ? budget - nact : 0;
+      int chunk_start = static_cast<int>(grp.size());
+      for (int s = 0; s < count; ++s) {
+        const Search& x = h->hs[s];
+        if (!x.trd || x.n <= kTrdPanel * q) continue;
+        const long long m = x.n - kTrdPanel * q;
+        const double share = static_cast<double>(m * m) / wsum;
+        int G = static_cast<int>(std::floor(share * static_cast<double>(spare))) + 1;
+        G = std::min(G, std::max(1, static_cast<int>(std::min(m / 16, m * m / 16384))));
+        if (static_cast<long long>(grp.size()) + G - chunk_start > budget) {
+          h->trd_chunks.push_back(TrdChunk{chunk_start, static_cast<int>(grp.size()) - chunk_start, q});
+          chunk_start = static_cast<int>(grp.size());
+        }
+        for (int r = 0; r < G; ++r) grp.push_back(make_int4(s, r, G, 0));
+      }
+      h->trd_chunks.push_back(TrdChunk{chunk_start, static_cast<int>(grp.size()) - chunk_start, q});
     }
-    h->trd_chunks.push_back(std::make_pair(chunk_start, static_cast<int>(grp.size()) - chunk_start));
     h->trd_grp_blocks = static_cast<int>(grp.size());
     // eigenvalues to find per decomposition of the whole batch: with more than
     // the GPU holds as 8-lane groups, plain bisection does the least work

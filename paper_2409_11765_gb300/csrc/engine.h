@@ -243,13 +243,19 @@ int tiles_trd_s2k_pack(int n);  // 64-row blocks of the reduction's trailing-upd
 int tiles_trd_s2k(int n);       // 128 x 64 tiles of its trailing update
 void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
+constexpr int kTrdPanel = 64;  // columns per panel of the tridiagonal reduction
+// One cooperative launch of the reduction: CTAs [first, first + count) of the
+// group table, all working on panel `panel`.
+struct TrdChunk {
+  int first, count, panel;
+};
 struct TrdMaps {
   TileMap tt, tbis, tsq, tbt, ozp, ozg;  // TK_TRD, TK_TRDBIS, TK_TRDSQ, TK_TRDBT, TK_TRDOZP, TK_TRDOZG
   TileMap btpack, btgram, bttfac, btrows, btcols, btupd, btfin;  // TK_BTPACK .. TK_BTFIN
   TileMap s2kp, s2k;  // TK_TRDS2KP, TK_TRDS2K
 };
 int launch_bt(Search* S, const TrdMaps& m, int max_n, cudaStream_t st);
-int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
+int launch_eig_trd(Search* S, const int4* grp, const TrdChunk* chunks, int nchunks, unsigned* bars,
                    int bar_count, int s0, int s1, const TrdMaps& tm, int max_n, int bis_lanes, cudaStream_t st,
                    cudaEvent_t* marks);
 

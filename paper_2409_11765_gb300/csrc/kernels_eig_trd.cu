@@ -91,25 +91,30 @@ __device__ bool trd_group_sync(unsigned* ctr, unsigned target, int* err, int* sh
 // is only read: the current matrix is A - V W^T - W V^T with V the panel's
 // reflectors so far (columns k0.. of EX) and W (columns 0.. of EG) built step
 // by step; after the panel the trailing part of A takes that rank-2 kPnb
-// update as one FP64-accurate product on the tensor cores (k_trd_s2k_*).
+// update as FP64-accurate products on the tensor cores (k_trd_s2k_*).
 // CTA blockIdx.x works for search grp[b].x as member r = grp[b].y of a group
-// of G = grp[b].z CTAs: it owns the columns j with j mod G = r (the
-// symmetric product) and the 32-row chunks c with c mod G = r (the corrected
-// column and its partial sums). Step k (panel column j = k - k0):
-//   A. w of step k - 1 on the own rows; column k of the current matrix,
-//      c = A(:, k) - V W(k, :)^T - W V(k, :)^T, on the own rows below the
-//      diagonal (to cbuf); partial sums of |c(k+2:)|^2, W^T c(k+2:) and
-//      V^T c(k+2:);                                              group barrier
-//   B. (every CTA) the reflector of c from the summed partials, its vector v,
-//      u_W = W^T v and u_V = V^T v; on the own columns
-//      p(j') = tau (A(:, j')^T v - V(j', :) u_W - W(j', :) u_V), and the
-//      partial p . v;                                             group barrier
-// and w = p - (tau / 2)(p . v) v completes at the next step's A. Barrier m
-// (1-based, counted over the whole reduction) waits for G m arrivals: the
-// one after the symmetrisation is m = 1, step k's are 2k + 2 and 2k + 3.
+// of G = grp[b].z CTAs: it owns the columns j with j mod G = r and the 32-row
+// chunks c with c mod G = r. Step k (panel column j = k - k0) in two phases:
+//   A. with u_W = W^T v, u_V = V^T v (the previous step's v, from the previous
+//      phase B) and q = A v on the own rows, the previous step's
+//      p = tau (q - V u_W - W u_V) and w = p - (tau / 2)(p . v) v, where
+//      p . v = tau (q . v - 2 u_W . u_V); then, in the same pass over the own
+//      rows, column k of the current matrix, c = A(:, k) - V W(k, :)^T -
+//      W V(k, :)^T (to cbuf), and the partial sum of |c(k+2:)|^2;
+//                                                               group barrier
+//   B. (every CTA) the reflector of c and its vector v; on the own columns
+//      q(j') = A(:, j')^T v (to qbuf) and the partial q . v; on the own
+//      columns of [W V] (2j of them), u = [W V]^T v over rows k+1..;
+//                                                               group barrier
+// The group (its size may differ from panel to panel) counts its barriers
+// from the start of the panel: barrier m waits for G m arrivals; in panel 0
+// the one after the symmetrisation is m = 1 and step k's are 2k + 2 and
+// 2k + 3, in the others step k's are 2(k - k0) + 1 and 2(k - k0) + 2.
 // Dynamic shared memory: v (n doubles).
 // --------------------------------------------------------------------------
-__global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp, int q) {
+constexpr int kUbuf = 2 * kPnb;  // u_W then u_V at the start of Search::EH, then the partial sums
+
+__global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* grp, int q) {
   extern __shared__ double vsm[];
   __shared__ double sVk[kPnb], sWk[kPnb], su[2 * kPnb];
   __shared__ double red[kTrdNT / 32 + 8];
@@ -131,9 +136,10 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
   double* e = tv(s, TV_E);
   double* tau = tv(s, TV_TAU);
   double* cbuf = tv(s, TV_P0);
-  double* pbuf = tv(s, TV_P1);
-  double* pvp = tv(s, TV_SD);  // per-CTA p . v
-  double* part = s.EH;         // per-CTA partial sums, kPartStride apart
+  double* qbuf = tv(s, TV_P1);
+  double* pvp = tv(s, TV_SD);         // per-CTA partial q . v
+  double* ubuf = s.EH;                // u_W (kPnb), u_V (kPnb)
+  double* part = s.EH + kUbuf;        // per-CTA partial |c|^2, kPartStride apart
   unsigned* bar = s.trd_bar;
   auto barrier = [&](unsigned m) -> bool {
     if (G > 1) return trd_group_sync(bar, static_cast<unsigned>(G) * m, s.err, &sh_ok);
@@ -151,38 +157,85 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
     const int c0 = row >> 5;
     return c0 + ((r - c0 % G) % G + G) % G;
   };
-  // w of step k - 1 (panel column j - 1) on the own rows i >= k
-  auto finish_w = [&](int k, int j, double tprev) {
-    if (warp == 0) {
-      double sp = 0.0;
-      for (int c = lane; c < G; c += 32) sp += __ldcg(&pvp[c]);
-      sp = warp_sum_xor(sp);
-      if (lane == 0) red[NW] = 0.5 * tprev * sp;
+  const unsigned mbase = q == 0 ? 1u : 0u;
+  double tprev = 0.0;
+  // Phase A of step k (j = k - k0); with last, only the previous step's w on
+  // the own rows i >= k (the end of the panel). Returns the partial |c|^2.
+  auto phase_a = [&](int k, int j, bool last) -> double {
+    const int jp = j - 1;  // columns of W and V before the previous step
+    if (j > 0) {
+      for (int l = tid; l < jp; l += kTrdNT) {
+        su[l] = __ldcg(&ubuf[l]);
+        su[kPnb + l] = __ldcg(&ubuf[kPnb + l]);
+        sVk[l] = __ldcg(&Hv[k + L * (k0 + l)]);
+        sWk[l] = __ldcg(&Wp[k + L * l]);
+      }
+      __syncthreads();
+      if (warp == 0) {  // q . v, u_W . u_V and the row-k correction, lanes in fixed order
+        double sq = 0.0, uu = 0.0, ck = 0.0;
+        for (int c = lane; c < G; c += 32) sq += __ldcg(&pvp[c]);
+        for (int l = lane; l < jp; l += 32) {
+          uu = fma(su[l], su[kPnb + l], uu);
+          ck = fma(sVk[l], su[l], fma(sWk[l], su[kPnb + l], ck));
+        }
+        sq = warp_sum_xor(sq);
+        uu = warp_sum_xor(uu);
+        ck = warp_sum_xor(ck);
+        if (lane == 0) {
+          const double half = 0.5 * tprev * tprev * (sq - 2.0 * uu);  // (tau / 2) p . v
+          const double pk = tprev * (__ldcg(&qbuf[k]) - ck);
+          sVk[jp] = 1.0;                // v_{k-1}(k)
+          sWk[jp] = fma(-half, 1.0, pk);  // w_{k-1}(k)
+          red[NW] = half;
+        }
+      }
+      __syncthreads();
     }
-    __syncthreads();
-    const double half = red[NW];
+    const double half = j > 0 ? red[NW] : 0.0;
+    double nrm = 0.0;
     for (int c = first_chunk(k) + G * warp; 32 * c < n; c += G * NW) {
       const int i = 32 * c + lane;
-      if (i >= k && i < n) Wp[i + L * (j - 1)] = fma(-half, vsm[i], __ldcg(&pbuf[i]));
+      if (i < k || i >= n) continue;
+      double pc = 0.0;  // V u_W + W u_V (previous step), then the column correction
+      double cc = 0.0;
+      int l = 0;
+      for (; l + 8 <= jp; l += 8) {  // eight columns' loads in flight
+        double hv[8], wv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          hv[u] = __ldcg(&Hv[i + L * (k0 + l + u)]);
+          wv[u] = __ldcg(&Wp[i + L * (l + u)]);
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+          pc = fma(hv[u], su[l + u], fma(wv[u], su[kPnb + l + u], pc));
+          cc = fma(hv[u], sWk[l + u], fma(wv[u], sVk[l + u], cc));
+        }
+      }
+      for (; l < jp; ++l) {
+        const double hv = __ldcg(&Hv[i + L * (k0 + l)]), wv = __ldcg(&Wp[i + L * l]);
+        pc = fma(hv, su[l], fma(wv, su[kPnb + l], pc));
+        cc = fma(hv, sWk[l], fma(wv, sVk[l], cc));
+      }
+      if (j > 0) {
+        const double vi = vsm[i];  // v_{k-1}(i)
+        const double wi = fma(-half, vi, tprev * (__ldcg(&qbuf[i]) - pc));
+        Wp[i + L * jp] = wi;
+        cc = fma(vi, sWk[jp], fma(wi, sVk[jp], cc));
+      }
+      if (!last && i > k) {
+        const double ci = __ldcg(&A[i + L * k]) - cc;
+        vsm[i] = ci;
+        cbuf[i] = ci;
+        if (i >= k + 2) nrm = fma(ci, ci, nrm);
+      }
     }
-    return half;
+    return nrm;
   };
-  double tprev = 0.0;
   for (int k = k0; k < k1; ++k) {
     const int j = k - k0;
     // ---------------- A ----------------
-    if (j > 0) {
-      const double half = finish_w(k, j, tprev);
-      if (tid == 0) {
-        sVk[j - 1] = 1.0;                                // v_{k-1}(k)
-        sWk[j - 1] = fma(-half, 1.0, __ldcg(&pbuf[k]));  // w_{k-1}(k)
-      }
-    }
-    for (int l = tid; l + 1 < j; l += kTrdNT) {  // row k of the older columns
-      sVk[l] = __ldcg(&Hv[k + L * (k0 + l)]);
-      sWk[l] = __ldcg(&Wp[k + L * l]);
-    }
-    __syncthreads();
+    double nrm = phase_a(k, j, false);
     if (k == n - 1) {  // the last diagonal entry
       if (r == 0 && tid == 0) {
         double acc = __ldcg(&A[k + L * k]);
@@ -191,50 +244,15 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
       }
       return;
     }
-    double nrm = 0.0;
-    for (int c = first_chunk(k + 1) + G * warp; 32 * c < n; c += G * NW) {
-      const int i = 32 * c + lane;
-      if (i > k && i < n) {
-        double ci = __ldcg(&A[i + L * k]);
-        int l = 0;
-        for (; l + 8 <= j; l += 8) {  // eight columns' loads in flight
-          double hv[8], wv[8];
-#pragma unroll
-          for (int u = 0; u < 8; ++u) {
-            hv[u] = __ldcg(&Hv[i + L * (k0 + l + u)]);
-            wv[u] = __ldcg(&Wp[i + L * (l + u)]);
-          }
-#pragma unroll
-          for (int u = 0; u < 8; ++u) ci = fma(-hv[u], sWk[l + u], fma(-wv[u], sVk[l + u], ci));
-        }
-        for (; l < j; ++l)
-          ci = fma(-__ldcg(&Hv[i + L * (k0 + l)]), sWk[l], fma(-__ldcg(&Wp[i + L * l]), sVk[l], ci));
-        vsm[i] = ci;
-        cbuf[i] = ci;
-        if (i >= k + 2) nrm = fma(ci, ci, nrm);
-      }
-    }
     nrm = warp_sum_xor(nrm);
     if (lane == 0) red[warp] = nrm;
     __syncthreads();
-    double* pr = part + static_cast<long long>(r) * kPartStride;
     if (tid == 0) {
       double a = 0.0;
       for (int w = 0; w < NW; ++w) a += red[w];
-      pr[0] = a;
+      part[static_cast<long long>(r) * kPartStride] = a;
     }
-    // W^T c and V^T c over the own rows i >= k + 2 (one warp per column)
-    for (int l = warp; l < 2 * j; l += NW) {
-      const double* col = l < j ? Wp + L * l : Hv + L * (k0 + l - j);
-      double acc = 0.0;
-      for (int c = first_chunk(k + 2); 32 * c < n; c += G) {
-        const int i = 32 * c + lane;
-        if (i >= k + 2 && i < n) acc = fma(__ldcg(&col[i]), vsm[i], acc);
-      }
-      acc = warp_sum_xor(acc);
-      if (lane == 0) pr[1 + l] = acc;
-    }
-    if (!barrier(2u * k + 2u)) return;
+    if (!barrier(mbase + 2u * j + 1u)) return;
     // ---------------- B ----------------
     if (warp == 0) {
       double a = 0.0;
@@ -242,29 +260,16 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
       a = warp_sum_xor(a);
       if (lane == 0) red[NW + 1] = a;
     }
-    for (int l = tid; l < 2 * j; l += kTrdNT) {
-      const double* pp = part + 1 + l;
-      double a = 0.0;
-      int c = 0;
-      for (; c + 8 <= G; c += 8) {  // the same order, eight loads in flight
-        double x[8];
-#pragma unroll
-        for (int u = 0; u < 8; ++u) x[u] = __ldcg(&pp[static_cast<long long>(c + u) * kPartStride]);
-#pragma unroll
-        for (int u = 0; u < 8; ++u) a += x[u];
-      }
-      for (; c < G; ++c) a += __ldcg(&pp[static_cast<long long>(c) * kPartStride]);
-      su[l] = a;
-    }
     if (tid == 32) {  // the diagonal entry of column k
       double acc = __ldcg(&A[k + L * k]);
       for (int l = 0; l < j; ++l) acc = fma(-2.0 * sVk[l], sWk[l], acc);
       red[NW + 2] = acc;
     }
+    if (tid == 64) red[NW + 5] = __ldcg(&cbuf[k + 1]);  // alpha
     __syncthreads();
     if (tid == 0) {
       const double xn2 = red[NW + 1];
-      const double alpha = __ldcg(&cbuf[k + 1]);
+      const double alpha = red[NW + 5];
       double t = 0.0, beta = alpha, scale = 0.0;
       if (xn2 > 0.0) {
         beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
@@ -282,16 +287,13 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
     __syncthreads();
     const double t = red[NW], scale = red[NW + 3];
     for (int i = k + 1 + tid; i < n; i += kTrdNT) vsm[i] = (i == k + 1) ? 1.0 : __ldcg(&cbuf[i]) * scale;
-    for (int l = tid; l < j; l += kTrdNT) {
-      su[l] = fma(scale, su[l], __ldcg(&Wp[(k + 1) + L * l]));                  // u_W
-      su[j + l] = fma(scale, su[j + l], __ldcg(&Hv[(k + 1) + L * (k0 + l)]));  // u_V
-    }
     __syncthreads();
     for (int c = first_chunk(k + 1) + G * warp; 32 * c < n; c += G * NW) {
       const int i = 32 * c + lane;
       if (i > k && i < n) Hv[i + L * k] = vsm[i];
     }
-    // own columns j' >= k + 1, two per warp at a time
+    // own columns j' >= k + 1 of A, two per warp at a time, then the own
+    // columns of [W V] (index j + l' ... over the 2j of them, l' mod G = r)
     const int m0 = (k + 1 > r) ? (k + 1 - r + G - 1) / G : 0;
     double pv = 0.0;
     for (int m = m0 + warp;; m += 2 * NW) {
@@ -303,15 +305,16 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
       const double* A2 = A + L * j2c;
       double q1 = 0.0, q2 = 0.0;
       int i = k + 1 + lane;
-      for (; i + 96 < n; i += 128) {
-        double a1[4], a2[4];
+      constexpr int U = 8;  // rows per lane in flight, two columns
+      for (; i + 32 * (U - 1) < n; i += 32 * U) {
+        double a1[U], a2[U];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           a1[u] = A1[i + 32 * u];
           a2[u] = two ? A2[i + 32 * u] : 0.0;
         }
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
+        for (int u = 0; u < U; ++u) {
           const double vi = vsm[i + 32 * u];
           q1 = fma(a1[u], vi, q1);
           q2 = fma(a2[u], vi, q2);
@@ -322,21 +325,23 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
         q1 = fma(A1[i], vi, q1);
         if (two) q2 = fma(A2[i], vi, q2);
       }
-      for (int l = lane; l < j; l += 32) {
-        q1 = fma(-__ldcg(&Hv[j1 + L * (k0 + l)]), su[l], fma(-__ldcg(&Wp[j1 + L * l]), su[j + l], q1));
-        if (two)
-          q2 = fma(-__ldcg(&Hv[j2 + L * (k0 + l)]), su[l], fma(-__ldcg(&Wp[j2 + L * l]), su[j + l], q2));
-      }
-      q1 = t * warp_sum_xor(q1);
-      q2 = t * warp_sum_xor(q2);
+      q1 = warp_sum_xor(q1);
+      q2 = warp_sum_xor(q2);
       if (lane == 0) {
-        pbuf[j1] = q1;
+        qbuf[j1] = q1;
         pv = fma(q1, vsm[j1], pv);
         if (two) {
-          pbuf[j2] = q2;
+          qbuf[j2] = q2;
           pv = fma(q2, vsm[j2], pv);
         }
       }
+    }
+    for (int x = r + G * warp; x < 2 * j; x += G * NW) {  // u = [W V]^T v over rows k+1..
+      const double* col = x < j ? Wp + L * x : Hv + L * (k0 + x - j);
+      double acc = 0.0;
+      for (int i = k + 1 + lane; i < n; i += 32) acc = fma(__ldcg(&col[i]), vsm[i], acc);
+      acc = warp_sum_xor(acc);
+      if (lane == 0) ubuf[x < j ? x : kPnb + x - j] = acc;
     }
     if (lane == 0) red[warp] = pv;
     __syncthreads();
@@ -345,11 +350,11 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_panel(Search* S, const int4* grp
       for (int w = 0; w < NW; ++w) sp += red[w];
       pvp[r] = sp;
     }
-    if (!barrier(2u * k + 3u)) return;
+    if (!barrier(mbase + 2u * j + 2u)) return;
     tprev = t;
   }
   // the panel's last w (its last step was a full one: k1 < n)
-  finish_w(k1, k1 - k0, tprev);
+  phase_a(k1, k1 - k0, true);
 }
 
 // The trailing update after panel q: A(k1:, k1:) -= V W^T + W V^T (rows and
@@ -1152,7 +1157,7 @@ void trd_set_attributes(int max_n) {
 // after each stage (reduction, eigenvalues, inverse iteration, Gram-Schmidt in
 // clusters, orthogonalisation, back-transformation), for the per-stage times
 // of the profiling mode.
-int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks, int nchunks, unsigned* bars,
+int launch_eig_trd(Search* S, const int4* grp, const TrdChunk* chunks, int nchunks, unsigned* bars,
                    int bar_count, int s0, int s1, const TrdMaps& tm, int max_n, int bis_lanes, cudaStream_t st,
                    cudaEvent_t* marks) {
   if (nchunks <= 0 || s1 <= s0) return 0;
@@ -1161,29 +1166,31 @@ int launch_eig_trd(Search* S, const int4* grp, const std::pair<int, int>* chunks
     if (marks) cudaEventRecord(marks[k], st);
   };
   mark(0);
-  cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count, st);
-  const int panels = ceil_div(max_n, kPnb);
-  for (int q = 0; q < panels; ++q) {
-    for (int c = 0; c < nchunks; ++c) {
-      if (chunks[c].second <= 0) continue;
-      cudaLaunchConfig_t cfg = {};
-      cfg.gridDim = dim3(chunks[c].second);
-      cfg.blockDim = dim3(kTrdNT);
-      cfg.dynamicSmemBytes = trd_reduce_smem(max_n);
-      cfg.stream = st;
-      cudaLaunchAttribute attr[1];
-      attr[0].id = cudaLaunchAttributeCooperative;
-      attr[0].val.cooperative = 1;
-      cfg.attrs = attr;
-      cfg.numAttrs = 1;
-      cudaLaunchKernelEx(&cfg, k_trd_panel, S, grp + chunks[c].first, q);
-      ++nl;
+  int q_prev = -1;
+  for (int c = 0; c < nchunks; ++c) {
+    const int q = chunks[c].panel;
+    if (q != q_prev) {
+      if (q_prev >= 0 && tm.s2kp.total > 0 && tm.s2k.total > 0) {  // the previous panel's trailing update
+        k_trd_s2k_pack<<<tm.s2kp.total, kOzNT, 0, st>>>(S, tm.s2kp, q_prev);
+        k_trd_s2k<<<tm.s2k.total, kOzNT, kOzSmem, st>>>(S, tm.s2k, q_prev);
+        nl += 2;
+      }
+      cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count, st);  // the group barriers restart per panel
+      q_prev = q;
     }
-    if (q + 1 < panels && tm.s2kp.total > 0 && tm.s2k.total > 0) {
-      k_trd_s2k_pack<<<tm.s2kp.total, kOzNT, 0, st>>>(S, tm.s2kp, q);
-      k_trd_s2k<<<tm.s2k.total, kOzNT, kOzSmem, st>>>(S, tm.s2k, q);
-      nl += 2;
-    }
+    if (chunks[c].count <= 0) continue;
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(chunks[c].count);
+    cfg.blockDim = dim3(kTrdNT);
+    cfg.dynamicSmemBytes = trd_reduce_smem(max_n);
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    cudaLaunchKernelEx(&cfg, k_trd_panel, S, grp + chunks[c].first, q);
+    ++nl;
   }
   mark(1);
   k_trd_blocks<<<s1 - s0, kTrdNT, 0, st>>>(S, s0);

@@ -60,7 +60,7 @@ __device__ __forceinline__ int* ti(const Search& s, int which) {
 // panel), with np the padded n.
 // --------------------------------------------------------------------------
 constexpr int kBtNb = 128;  // reflectors per panel of the back-transformation
-constexpr int kPnb = 64;    // columns per panel of the reduction
+constexpr int kPnb = kTrdPanel;  // columns per panel of the reduction
 constexpr int kPartStride = 2 * kPnb + 8;  // per-CTA partial sums of a reduction step
 // Back-transformation: blocked on the tensor cores above this size, one
 // register-resident column per warp in FP64 at and below it (where the
