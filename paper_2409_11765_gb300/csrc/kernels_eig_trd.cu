@@ -494,7 +494,20 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_blocks(Search* S, int s0) {
     es[i] = x;
     e2[i] = x * x;
   }
+  // d and e^2 scaled by a power of two (|d| <= 1) in FP32 for the first
+  // bisection steps (the reduction's buffers TV_P0 and TV_P1 are free now)
+  const double scl = tn > 0.0 ? exp2(-static_cast<double>(ilogb(tn) + 1)) : 1.0;
+  float* d32 = reinterpret_cast<float*>(tv(s, TV_P0));
+  float* e32 = reinterpret_cast<float*>(tv(s, TV_P1));
+  for (int i = threadIdx.x; i < n; i += kTrdNT) {
+    d32[i] = static_cast<float>(d[i] * scl);
+    if (i + 1 < n) {
+      const double x = fabs(e[i]) <= split ? 0.0 : e[i] * scl;
+      e32[i] = static_cast<float>(x * x);
+    }
+  }
   if (threadIdx.x == 0) {
+    sc[7] = scl;
     sc[0] = tn;
     sc[1] = DBL_MIN * fmax(1.0, em * em);
     sc[2] = split;
@@ -525,9 +538,11 @@ constexpr int kTrdBisLanes = 8;
 int tiles_trd(int n) { return ceil_div(n, kTrdTT); }
 int tiles_trd_bis(int n) { return ceil_div(n * kTrdBisLanes, kTrdTT); }
 
+// 1 / q from the FP32 reciprocal and two Newton steps inside 2^-99 < |q| <
+// 2^99 (exponent tested on the integer pattern), the division elsewhere.
 __device__ __forceinline__ double fast_rcp(double q) {
-  const double aq = fabs(q);
-  if (aq > 1e-30 && aq < 1e30) {
+  const int ex = (__double2hiint(q) >> 20) & 0x7FF;
+  if (ex > 1023 - 99 && ex < 1023 + 99) {
     double r = static_cast<double>(__frcp_rn(static_cast<float>(q)));
     r = r * fma(-q, r, 2.0);
     return r * fma(-q, r, 2.0);
@@ -535,6 +550,44 @@ __device__ __forceinline__ double fast_rcp(double q) {
   return 1.0 / q;
 }
 
+// Sturm count: eigenvalues of block [b0, b1) below x (pivots of magnitude at
+// most pivmin replaced by -pivmin; |q| and pivmin compared as ordered bit
+// patterns, the sign read from the sign bit).
+__device__ __forceinline__ int sturm64(const double* d, const double* e2, int b0, int b1, double x, double pivmin) {
+  const long long pb = __double_as_longlong(pivmin);
+  int cnt = 0;
+  double qq = d[b0] - x;
+  if ((__double_as_longlong(qq) & 0x7FFFFFFFFFFFFFFFLL) <= pb) qq = -pivmin;
+  cnt += static_cast<int>(static_cast<unsigned long long>(__double_as_longlong(qq)) >> 63);
+  for (int j = b0 + 1; j < b1; ++j) {
+    qq = (d[j] - x) - e2[j - 1] * fast_rcp(qq);
+    if ((__double_as_longlong(qq) & 0x7FFFFFFFFFFFFFFFLL) <= pb) qq = -pivmin;
+    cnt += static_cast<int>(static_cast<unsigned long long>(__double_as_longlong(qq)) >> 63);
+  }
+  return cnt;
+}
+
+// The same in FP32 on the scaled copies (|d| <= 1).
+__device__ __forceinline__ int sturm32(const float* d, const float* e2, int b0, int b1, float x) {
+  constexpr float piv = 0x1p-90f;
+  int cnt = 0;
+  float qq = d[b0] - x;
+  if (fabsf(qq) <= piv) qq = -piv;
+  cnt += qq < 0.0f;
+  for (int j = b0 + 1; j < b1; ++j) {
+    qq = (d[j] - x) - e2[j - 1] * __frcp_rn(qq);
+    if (fabsf(qq) <= piv) qq = -piv;
+    cnt += qq < 0.0f;
+  }
+  return cnt;
+}
+
+// Eigenvalue t of its block by bisection (LANES = 1) or multisection with
+// LANES points per step. First in FP32 on the scaled block down to a width
+// of 2^-19 ||T||; the bracket is then widened by 2^-18 ||T|| (eight times the
+// backward error of an FP32 Sturm count, ~10 eps32 ||T||), checked with two
+// FP64 counts (the whole Gershgorin interval again if the check fails) and
+// bisected in FP64 to 4 eps64 ||T||.
 template <int LANES>
 __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   int tile;
@@ -545,10 +598,13 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   const int q = threadIdx.x % LANES;
   const int t = tile * (kTrdTT / LANES) + threadIdx.x / LANES;
   if (t >= n) return;  // uniform across the lanes of a group
-  const unsigned gmask = static_cast<unsigned>((1ull << LANES) - 1) << ((threadIdx.x & 31) & ~(LANES - 1));
+  const int base = (threadIdx.x & 31) & ~(LANES - 1);
+  const unsigned gmask = static_cast<unsigned>((1ull << LANES) - 1) << base;
   const double* d = tv(s, TV_D);
   const double* es = tv(s, TV_ES);
   const double* e2 = tv(s, TV_E2);
+  const float* d32 = reinterpret_cast<const float*>(tv(s, TV_P0));
+  const float* e32 = reinterpret_cast<const float*>(tv(s, TV_P1));
   const double* sc = tv(s, TV_SCAL);
   double* lamb = tv(s, TV_LAMB);
   const int b0 = ti(s, TI_B0)[t], b1 = ti(s, TI_B1)[t];
@@ -556,7 +612,7 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
     if (q == 0) lamb[t] = d[t];
     return;
   }
-  const double tn = sc[0], pivmin = sc[1];
+  const double tn = sc[0], pivmin = sc[1], scl = sc[7];
   double gl = INFINITY, gu = -INFINITY;
   for (int j = b0; j < b1; ++j) {
     const double rad = (j > b0 ? fabs(es[j - 1]) : 0.0) + (j + 1 < b1 ? fabs(es[j]) : 0.0);
@@ -567,28 +623,45 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   const double fudge = 2.0 * kTrdEps * tn * (b1 - b0) + 2.0 * pivmin;
   double lo = gl - fudge, hi = gu + fudge;
   const int idx = t - b0;
+  // one multisection step on [lo, hi] from the counts of the LANES points
+  auto narrow = [&](auto& lo_, auto& hi_, int cnt, auto w) -> bool {
+    const unsigned le = __ballot_sync(gmask, cnt <= idx) & gmask;
+    const int qlo = le ? (31 - __clz(le)) - base : -1;
+    const auto nlo = qlo >= 0 ? lo_ + w * (qlo + 1) : lo_;
+    const auto nhi = qlo + 1 < LANES ? lo_ + w * (qlo + 2) : hi_;
+    if (!(nlo < nhi) || (nlo == lo_ && nhi == hi_)) return false;
+    lo_ = nlo;
+    hi_ = nhi;
+    return true;
+  };
+  if (tn > 0.0) {
+    float lo32 = static_cast<float>(lo * scl), hi32 = static_cast<float>(hi * scl);
+    for (int it = 0; it < 40 && hi32 - lo32 > 0x1p-19f; ++it) {
+      const float w = (hi32 - lo32) / (LANES + 1);
+      if (!narrow(lo32, hi32, sturm32(d32, e32, b0, b1, lo32 + w * (q + 1)), w)) break;
+    }
+    const double margin = 0x1p-18 * tn;
+    const double lo2 = fmax(lo, static_cast<double>(lo32) / scl - margin);
+    const double hi2 = fmin(hi, static_cast<double>(hi32) / scl + margin);
+    // lane 0 checks that lo2 is left of the eigenvalue, lane 1 (or lane 0)
+    // that hi2 is right of it
+    bool ok = true;
+    if (LANES == 1) {
+      ok = sturm64(d, e2, b0, b1, lo2, pivmin) <= idx && sturm64(d, e2, b0, b1, hi2, pivmin) > idx;
+    } else {
+      bool mine = true;
+      if (q == 0) mine = sturm64(d, e2, b0, b1, lo2, pivmin) <= idx;
+      if (q == 1) mine = sturm64(d, e2, b0, b1, hi2, pivmin) > idx;
+      ok = (__ballot_sync(gmask, !mine) & gmask) == 0;
+    }
+    if (ok && lo2 < hi2) {
+      lo = lo2;
+      hi = hi2;
+    }
+  }
   for (int it = 0; it < 160 && hi - lo > atol; ++it) {
     const double w = (hi - lo) / (LANES + 1);
-    const double x = lo + w * (q + 1);
-    int cnt = 0;
-    double qq = d[b0] - x;
-    if (fabs(qq) <= pivmin) qq = -pivmin;
-    cnt += qq < 0.0;
-    for (int j = b0 + 1; j < b1; ++j) {
-      qq = (d[j] - x) - e2[j - 1] * fast_rcp(qq);
-      if (fabs(qq) <= pivmin) qq = -pivmin;
-      cnt += qq < 0.0;
-    }
-    // points with count <= idx lie left of the eigenvalue: the bracket
-    // becomes [x_qlo, x_qlo+1] for the rightmost such point qlo
-    const unsigned le = __ballot_sync(gmask, cnt <= idx) & gmask;
-    const int base = (threadIdx.x & 31) & ~(LANES - 1);
-    const int qlo = le ? (31 - __clz(le)) - base : -1;
-    const double nlo = qlo >= 0 ? lo + w * (qlo + 1) : lo;
-    const double nhi = qlo + 1 < LANES ? lo + w * (qlo + 2) : hi;
-    if (!(nlo < nhi) || (nlo == lo && nhi == hi)) break;
-    lo = nlo;
-    hi = nhi;
+    if (!narrow(lo, hi, sturm64(d, e2, b0, b1, lo + w * (q + 1), pivmin), w)) break;
   }
   if (q == 0) lamb[t] = 0.5 * (lo + hi);
 }
