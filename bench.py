@@ -391,12 +391,16 @@ def measure(args, wl, prec, world, rank, dist, want_clocks, eig_method, secondar
 
 def stage_flops(decomps):
     """Algorithmic FP64 flops of the eigendecompositions per stage, from the
-    decompositions done: Householder reduction 4/3 n^3, back-transformation
-    2 n^3 (LAPACK's counts for dsytrd and dormtr); the eigenvalue and
+    decompositions done. Householder reduction: of LAPACK's 4/3 n^3 for
+    dsytrd, the half left on the FP64 units, the symmetric products
+    A(k+1:, k+1:) v, 2 (n - k - 1)^2 at step k, 2/3 n^3 in all (the rank-2
+    trailing updates, the other 2/3 n^3, run on the tensor cores).
+    Back-transformation: 2 n^3 (dormtr's count) for n <= 512, where it runs in
+    FP64; above, on the tensor cores (0 FP64 flops). The eigenvalue and
     eigenvector stages are O(n^2) per decomposition and the Newton-Schulz
     orthogonalisation is not part of the minimal method (0)."""
-    red = sum(k * 4.0 / 3.0 * n ** 3 for n, k in decomps.items())
-    bt = sum(k * 2.0 * n ** 3 for n, k in decomps.items())
+    red = sum(k * 2.0 / 3.0 * n ** 3 for n, k in decomps.items())
+    bt = sum(k * 2.0 * n ** 3 for n, k in decomps.items() if n <= 512)
     return {"reduction": red, "backtransform": bt, "eigenvalues": 0.0, "eigenvectors": 0.0,
             "orthogonalisation": 0.0}
 
