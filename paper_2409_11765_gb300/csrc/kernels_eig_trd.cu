@@ -833,14 +833,16 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
   const int* b0a = ti(s, TI_B0);
   const int* b1a = ti(s, TI_B1);
   double* V = s.ET;
+  // work items: the chunks of at most kTrdClusMax vectors of every cluster of
+  // two or more (independent of one another), dealt round-robin to the warps
   int found = 0;
   for (int c = 0; c < n; ++c) {
-    if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;  // clusters of two or more
-    if ((found++ % (kTrdMgsCtas * kTrdNT / 32)) != warp) continue;
+    if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;
     int ce = c + 1;
     while (ce < n && cl0[ce] == c) ++ce;
     for (int cc = c; cc < ce; cc += kTrdClusMax)
-      cluster_mgs(V, L, cc, min(ce, cc + kTrdClusMax), b0a[c], b1a[c], lane);
+      if ((found++ % (kTrdMgsCtas * kTrdNT / 32)) == warp)
+        cluster_mgs(V, L, cc, min(ce, cc + kTrdClusMax), b0a[c], b1a[c], lane);
   }
 }
 
@@ -970,8 +972,7 @@ __global__ void __launch_bounds__(kOzNT, 1) k_trd_oz_gram(Search* S, TileMap tm,
         double m = 0.0;
         if (needed[h]) {
           const int ej = s.oze[j];
-          double g = (static_cast<double>(Wq[q]) + static_cast<double>(Lq[q])) * oz_pow2(ei + ej - 44);
-          if (ei <= kOzZeroExp || ej <= kOzZeroExp) g = 0.0;
+          const double g = oz_value(Wq[q], Lq[q], ei, ej);
           m = 0.5 * ((i == j ? 1.0 : 0.0) - g);
           dmax = fmax(dmax, fabs(m));
         }

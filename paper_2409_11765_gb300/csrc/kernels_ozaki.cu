@@ -64,8 +64,7 @@ __global__ void __launch_bounds__(kOzNT, 1) k_oz_gemm(const OzGemmJob* job, int*
       for (int q = 0; q < 32; ++q) {
         const int j = jb + q;
         if (j >= J.N) continue;
-        double v = (static_cast<double>(W[q]) + static_cast<double>(L[q])) * oz_pow2(ea + J.eb[j] - 44);
-        if (ea <= kOzZeroExp || J.eb[j] <= kOzZeroExp) v = 0.0;
+        const double v = oz_value(W[q], L[q], ea, J.eb[j]);
         double* cp = J.c + i + J.ldc * j;
         *cp = J.beta == 0.0 ? J.alpha * v : fma(J.alpha, v, J.beta * *cp);
       }

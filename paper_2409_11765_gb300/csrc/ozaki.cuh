@@ -171,11 +171,55 @@ __device__ __forceinline__ double oz_pow2(int e) {
   return ldexp(1.0, e);
 }
 
+// x 2^e as a double for an integer x, assembled on the bit pattern (the
+// leading bit found by clz, rounded to nearest even above 2^53): the same
+// value as double(x) * 2^e without FP64 arithmetic. Outside the normal range
+// it falls back to the FP64 operations.
+__device__ __forceinline__ double oz_i2d_scaled(long long x, int e) {
+  if (x == 0) return 0.0;
+  const unsigned long long sgn = static_cast<unsigned long long>(x) & 0x8000000000000000ull;
+  unsigned long long m = x < 0 ? 0ull - static_cast<unsigned long long>(x) : static_cast<unsigned long long>(x);
+  const int msb = 63 - __clzll(static_cast<long long>(m));
+  int ex = msb + e;
+  if (msb > 52) {
+    const int sh = msb - 52;
+    const unsigned long long rem = m & ((1ull << sh) - 1), half = 1ull << (sh - 1);
+    m >>= sh;
+    if (rem > half || (rem == half && (m & 1ull))) {
+      ++m;
+      if (m >> 53) {
+        m >>= 1;
+        ++ex;
+      }
+    }
+  } else {
+    m <<= (52 - msb);
+  }
+  if (ex < -1022 || ex > 1023) return static_cast<double>(x) * oz_pow2(e);
+  return __longlong_as_double(static_cast<long long>(sgn | (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                     (m & 0xFFFFFFFFFFFFFull)));
+}
+
+// f 2^e as a double for a float f, on the bit pattern (exact; zero for a
+// zero or subnormal f), the FP64 operations outside the normal range.
+__device__ __forceinline__ double oz_f2d_scaled(float f, int e) {
+  const unsigned u = __float_as_uint(f);
+  const int fe = static_cast<int>((u >> 23) & 0xFF);
+  if (fe == 0) return 0.0;
+  const int ex = fe - 127 + e;
+  if (ex < -1022 || ex > 1023) return static_cast<double>(f) * oz_pow2(e);
+  return __longlong_as_double(static_cast<long long>((static_cast<unsigned long long>(u >> 31) << 63) |
+                                                     (static_cast<unsigned long long>(ex + 1023) << 52) |
+                                                     (static_cast<unsigned long long>(u & 0x7FFFFFu) << 29)));
+}
+
 // The FP64 value of an output element from its tile sums (oz_tile) and the
-// exponents of its row of A and its row of B.
+// exponents of its row of A and its row of B: (W + L) 2^(eA + eB - 44), both
+// terms scaled exactly, one FP64 addition.
 __device__ __forceinline__ double oz_value(long long W, float L, int ea, int eb) {
   if (ea <= kOzZeroExp || eb <= kOzZeroExp) return 0.0;
-  return (static_cast<double>(W) + static_cast<double>(L)) * oz_pow2(ea + eb - 44);
+  const int e = ea + eb - 44;
+  return oz_i2d_scaled(W, e) + oz_f2d_scaled(L, e);
 }
 
 // --------------------------------------------------------------------------
