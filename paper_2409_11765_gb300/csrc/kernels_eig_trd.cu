@@ -497,13 +497,20 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_blocks(Search* S, int s0) {
   // d and e^2 scaled by a power of two (|d| <= 1) in FP32 for the first
   // bisection steps (the reduction's buffers TV_P0 and TV_P1 are free now)
   const double scl = tn > 0.0 ? exp2(-static_cast<double>(ilogb(tn) + 1)) : 1.0;
+  // as pairs hi + lo of floats (hi the rounded value, lo the rounded rest):
+  // d at TV_P0 (hi, then lo from ldn on), e^2 at TV_P1 likewise
   float* d32 = reinterpret_cast<float*>(tv(s, TV_P0));
   float* e32 = reinterpret_cast<float*>(tv(s, TV_P1));
+  const long long L2 = s.ldn;
   for (int i = threadIdx.x; i < n; i += kTrdNT) {
-    d32[i] = static_cast<float>(d[i] * scl);
+    const double ds = d[i] * scl;
+    d32[i] = static_cast<float>(ds);
+    d32[L2 + i] = static_cast<float>(ds - static_cast<double>(d32[i]));
     if (i + 1 < n) {
       const double x = fabs(e[i]) <= split ? 0.0 : e[i] * scl;
-      e32[i] = static_cast<float>(x * x);
+      const double x2 = x * x;
+      e32[i] = static_cast<float>(x2);
+      e32[L2 + i] = static_cast<float>(x2 - static_cast<double>(e32[i]));
     }
   }
   if (threadIdx.x == 0) {
@@ -582,12 +589,71 @@ __device__ __forceinline__ int sturm32(const float* d, const float* e2, int b0, 
   return cnt;
 }
 
+// The same in double-float arithmetic (each value a pair hi + lo of floats,
+// ~48 significant bits; error-free sums and products from FMA) on the scaled
+// pairs: d at d32 / d32 + ldn, e^2 at e32 / e32 + ldn, x = xh + xl.
+__device__ __forceinline__ void df_two_sum(float a, float b, float& s, float& e) {
+  s = __fadd_rn(a, b);
+  const float bb = __fsub_rn(s, a);
+  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+}
+__device__ __forceinline__ int sturm_df(const float* dh, const float* dl, const float* eh, const float* el,
+                                        int b0, int b1, float xh, float xl) {
+  constexpr float piv = 0x1p-90f;
+  int cnt = 0;
+  float qh, ql;
+  {
+    float s, e;
+    df_two_sum(dh[b0], -xh, s, e);
+    e = __fadd_rn(e, __fsub_rn(dl[b0], xl));
+    qh = __fadd_rn(s, e);
+    ql = __fsub_rn(e, __fsub_rn(qh, s));
+  }
+  if (fabsf(qh) <= piv) {
+    qh = -piv;
+    ql = 0.0f;
+  }
+  cnt += qh < 0.0f;
+  for (int j = b0 + 1; j < b1; ++j) {
+    // t = d_j - x
+    float th, tl;
+    {
+      float s, e;
+      df_two_sum(dh[j], -xh, s, e);
+      e = __fadd_rn(e, __fsub_rn(dl[j], xl));
+      th = __fadd_rn(s, e);
+      tl = __fsub_rn(e, __fsub_rn(th, s));
+    }
+    // u = e2 / q: leading quotient, then the rest from the exact residual
+    const float e2h = eh[j - 1], e2l = el[j - 1];
+    const float uh = __fdiv_rn(e2h, qh);
+    const float p = __fmul_rn(uh, qh);
+    const float pe = __fmaf_rn(uh, qh, -p);
+    const float r = __fadd_rn(__fsub_rn(__fsub_rn(e2h, p), pe), __fmaf_rn(-uh, ql, e2l));
+    const float ul = __fdiv_rn(r, qh);
+    // q = t - u
+    float s, e;
+    df_two_sum(th, -uh, s, e);
+    e = __fadd_rn(e, __fsub_rn(tl, ul));
+    qh = __fadd_rn(s, e);
+    ql = __fsub_rn(e, __fsub_rn(qh, s));
+    if (fabsf(qh) <= piv) {
+      qh = -piv;
+      ql = 0.0f;
+    }
+    cnt += qh < 0.0f;
+  }
+  return cnt;
+}
+
 // Eigenvalue t of its block by bisection (LANES = 1) or multisection with
-// LANES points per step. First in FP32 on the scaled block down to a width
-// of 2^-19 ||T||; the bracket is then widened by 2^-18 ||T|| (eight times the
-// backward error of an FP32 Sturm count, ~10 eps32 ||T||), checked with two
-// FP64 counts (the whole Gershgorin interval again if the check fails) and
-// bisected in FP64 to 4 eps64 ||T||.
+// LANES points per step, in three precisions: FP32 on the scaled block down to
+// a width of 2^-19 ||T||, widened by 2^-18 ||T|| (eight times the backward
+// error of an FP32 Sturm count, ~10 eps32 ||T||); double-float down to
+// 2^-41 ||T||, widened by 2^-40 ||T|| (over ten times that of a double-float
+// count, ~10 2^-48 ||T||); each widened bracket checked with two counts of
+// the next precision (the previous bracket kept if the check fails), the
+// last step in FP64 to 4 eps64 ||T||.
 template <int LANES>
 __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   int tile;
@@ -634,27 +700,42 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
     hi_ = nhi;
     return true;
   };
+  // the two ends of a candidate bracket checked by the counts `cnt` (lane 0
+  // the left end, lane 1 the right one; one lane does both)
+  auto check = [&](auto cnt, double a, double b) -> bool {
+    if (LANES == 1) return cnt(a) <= idx && cnt(b) > idx;
+    bool mine = true;
+    if (q == 0) mine = cnt(a) <= idx;
+    if (q == 1) mine = cnt(b) > idx;
+    return (__ballot_sync(gmask, !mine) & gmask) == 0;
+  };
   if (tn > 0.0) {
+    const long long L2 = s.ldn;
+    // FP32
     float lo32 = static_cast<float>(lo * scl), hi32 = static_cast<float>(hi * scl);
     for (int it = 0; it < 40 && hi32 - lo32 > 0x1p-19f; ++it) {
       const float w = (hi32 - lo32) / (LANES + 1);
       if (!narrow(lo32, hi32, sturm32(d32, e32, b0, b1, lo32 + w * (q + 1)), w)) break;
     }
-    const double margin = 0x1p-18 * tn;
-    const double lo2 = fmax(lo, static_cast<double>(lo32) / scl - margin);
-    const double hi2 = fmin(hi, static_cast<double>(hi32) / scl + margin);
-    // lane 0 checks that lo2 is left of the eigenvalue, lane 1 (or lane 0)
-    // that hi2 is right of it
-    bool ok = true;
-    if (LANES == 1) {
-      ok = sturm64(d, e2, b0, b1, lo2, pivmin) <= idx && sturm64(d, e2, b0, b1, hi2, pivmin) > idx;
-    } else {
-      bool mine = true;
-      if (q == 0) mine = sturm64(d, e2, b0, b1, lo2, pivmin) <= idx;
-      if (q == 1) mine = sturm64(d, e2, b0, b1, hi2, pivmin) > idx;
-      ok = (__ballot_sync(gmask, !mine) & gmask) == 0;
+    auto cnt_df = [&](double xs) {  // x given scaled, in FP64
+      const float xh = static_cast<float>(xs);
+      return sturm_df(d32, d32 + L2, e32, e32 + L2, b0, b1, xh, static_cast<float>(xs - static_cast<double>(xh)));
+    };
+    double los = lo * scl, his = hi * scl;  // scaled bracket, FP64
+    {
+      const double a = fmax(los, static_cast<double>(lo32) - 0x1p-18), b = fmin(his, static_cast<double>(hi32) + 0x1p-18);
+      if (a < b && check(cnt_df, a, b)) {
+        los = a;
+        his = b;
+      }
     }
-    if (ok && lo2 < hi2) {
+    // double-float
+    for (int it = 0; it < 60 && his - los > 0x1p-41; ++it) {
+      const double w = (his - los) / (LANES + 1);
+      if (!narrow(los, his, cnt_df(los + w * (q + 1)), w)) break;
+    }
+    const double lo2 = fmax(lo, (los - 0x1p-40) / scl), hi2 = fmin(hi, (his + 0x1p-40) / scl);
+    if (lo2 < hi2 && check([&](double x) { return sturm64(d, e2, b0, b1, x, pivmin); }, lo2, hi2)) {
       lo = lo2;
       hi = hi2;
     }
