@@ -791,13 +791,24 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     CREATE_TRY(cudaGetDevice(&dev));
     CREATE_TRY(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     trd_set_attributes(h->max_n_trd);
-    const int per_sm = trd_reduce_blocks_per_sm(h->max_n_trd);
+    // the largest group of a search: at least 16 columns per CTA, and enough
+    // work per step to outweigh the group barriers ((n - 64 q)^2 / 16384)
+    auto gcap = [](long long m) { return std::max(1, static_cast<int>(std::min(m / 16, m * m / 16384))); };
+    // the unblocked form (one barrier per step) when every search can have its
+    // largest group at once: the GPU is then partly idle and a step's latency
+    // sets the time; the panel form otherwise
+    long long caps = 0;
+    for (int s = 0; s < count; ++s)
+      if (h->hs[s].trd) caps += gcap(h->hs[s].n);
+    const long long budget_u = static_cast<long long>(trd_reduce_blocks_per_sm(h->max_n_trd, 0)) * sms;
+    const bool blocked = caps > budget_u;
+    const int per_sm = trd_reduce_blocks_per_sm(h->max_n_trd, blocked ? 1 : 0);
     long long budget = static_cast<long long>(per_sm) * sms;
     if (budget < 1) {
       set_error(h, CMAES_EUNSUPPORTED, "the tridiagonal reduction cannot be resident on this device");
       return fail(CMAES_EUNSUPPORTED);
     }
-    // one group table per panel of kTrdPanel columns: the searches with
+    // the panel form: one group table per panel of kTrdPanel columns: the searches with
     // columns left in panel q share the resident CTAs in proportion to their
     // trailing work (n - kTrdPanel q)^2, each with at least one CTA and at most
     // (n - kTrdPanel q) / 16 and (n - kTrdPanel q)^2 / 16384 (enough work per
@@ -805,7 +816,15 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     // never split a group
     std::vector<int4> grp;
     h->trd_chunks.clear();
-    const int panels = ceil_div(h->max_n_trd, kTrdPanel);
+    if (!blocked) {
+      for (int s = 0; s < count; ++s) {
+        if (!h->hs[s].trd) continue;
+        const int G = gcap(h->hs[s].n);
+        for (int r = 0; r < G; ++r) grp.push_back(make_int4(s, r, G, 0));
+      }
+      h->trd_chunks.push_back(TrdChunk{0, static_cast<int>(grp.size()), -1});
+    }
+    const int panels = blocked ? ceil_div(h->max_n_trd, kTrdPanel) : 0;
     for (int q = 0; q < panels; ++q) {
       double wsum = 0.0;
       int nact = 0;
@@ -825,7 +844,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
         const long long m = x.n - kTrdPanel * q;
         const double share = static_cast<double>(m * m) / wsum;
         int G = static_cast<int>(std::floor(share * static_cast<double>(spare))) + 1;
-        G = std::min(G, std::max(1, static_cast<int>(std::min(m / 16, m * m / 16384))));
+        G = std::min(G, gcap(m));
         if (static_cast<long long>(grp.size()) + G - chunk_start > budget) {
           h->trd_chunks.push_back(TrdChunk{chunk_start, static_cast<int>(grp.size()) - chunk_start, q});
           chunk_start = static_cast<int>(grp.size());

@@ -237,15 +237,16 @@ int tiles_bt_cols(int n);    // 64-column tiles of a 128 x n product
 int tiles_bt_update(int n);  // 128 x 64 tiles of the largest panel's update
 int tiles_bt_final(int n);   // 8 columns per tile
 void bt_set_attributes();
-size_t trd_reduce_smem(int max_n);
-int trd_reduce_blocks_per_sm(int max_n);
+size_t trd_reduce_smem(int max_n, int blocked);
+int trd_reduce_blocks_per_sm(int max_n, int blocked);
 int tiles_trd_s2k_pack(int n);  // 64-row blocks of the reduction's trailing-update operands
 int tiles_trd_s2k(int n);       // 128 x 64 tiles of its trailing update
 void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
 constexpr int kTrdPanel = 64;  // columns per panel of the tridiagonal reduction
 // One cooperative launch of the reduction: CTAs [first, first + count) of the
-// group table, all working on panel `panel`.
+// group table, all working on panel `panel` (-1: the unblocked form, the
+// whole reduction in one launch).
 struct TrdChunk {
   int first, count, panel;
 };

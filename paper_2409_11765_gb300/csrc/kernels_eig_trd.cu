@@ -357,6 +357,188 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
   phase_a(k1, k1 - k0, true);
 }
 
+// --------------------------------------------------------------------------
+// 1'. The unblocked reduction, for handles whose searches leave the GPU
+// partly idle (each group at its largest size): then a step's latency, not
+// the FP64 work, sets the time, and this form has one group barrier per step
+// (against two in the panel form). Golub & Van Loan §8.3.1: per step every
+// CTA forms the reflector of column k itself (the same fixed-order
+// arithmetic everywhere), then applies the pending rank-2 update
+// A <- A - v w^T - w v^T of the previous step to the columns it owns while it
+// accumulates p = tau A v for the new v: one pass over the trailing matrix.
+// CTA blockIdx.x works for search grp[b].x as member grp[b].y of a group of
+// grp[b].z CTAs; column j belongs to member j mod G, and within it to warp
+// (j div G) mod 8. Dynamic shared memory: v and w of the previous step and v
+// of the current one (3 n doubles).
+// --------------------------------------------------------------------------
+__global__ void __launch_bounds__(kTrdNT) k_trd_sytrd(Search* S, const int4* grp) {
+  extern __shared__ double tsm[];
+  __shared__ double red[kTrdNT / 32 + 8];
+  __shared__ int sh_ok;
+  const int4 g = grp[blockIdx.x];
+  Search& s = S[g.x];
+  if (!trd_due(s)) return;
+  const int n = s.n;
+  const long long L = s.ldn;
+  const int r = g.y, G = g.z;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  constexpr int NW = kTrdNT / 32;
+  double* W = s.EA;
+  double* Hv = s.EX;
+  const double* C = s.C;
+  double* d = tv(s, TV_D);
+  double* e = tv(s, TV_E);
+  double* tau = tv(s, TV_TAU);
+  double* pbuf = tv(s, TV_P0);  // two buffers: step k uses pbuf + (k & 1) L
+  double* sdot = tv(s, TV_SD);  // per-CTA partial p.v, two buffers of L / 2
+  unsigned* bar = s.trd_bar;
+  double* vprev = tsm;
+  double* wprev = tsm + n;
+  double* vcur = tsm + 2 * n;
+  // W = (C + C^T) / 2, owned columns only
+  for (int j = r; j < n; j += G)
+    for (int i = tid; i < n; i += kTrdNT) W[i + L * j] = 0.5 * (C[i + L * j] + C[j + L * i]);
+  for (int i = tid; i < n; i += kTrdNT) {
+    vprev[i] = 0.0;
+    wprev[i] = 0.0;
+  }
+  unsigned nb = 0;
+  if (G > 1) {
+    if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
+  } else {
+    __syncthreads();
+  }
+  for (int k = 0; k + 1 < n; ++k) {
+    // column k with the pending update of step k - 1
+    for (int i = k + tid; i < n; i += kTrdNT)
+      vcur[i] = fma(-wprev[i], vprev[k], fma(-vprev[i], wprev[k], __ldcg(&W[i + L * k])));
+    __syncthreads();
+    // its reflector (warp 0, fixed-order sum)
+    if (warp == 0) {
+      double part = 0.0;
+      for (int i = k + 2 + lane; i < n; i += 32) part = fma(vcur[i], vcur[i], part);
+      const double xn2 = warp_sum_xor(part);
+      if (lane == 0) {
+        const double alpha = vcur[k + 1];
+        double t = 0.0, beta = alpha, scale = 0.0;
+        if (xn2 > 0.0) {
+          beta = -copysign(sqrt(fma(alpha, alpha, xn2)), alpha);
+          t = (beta - alpha) / beta;
+          scale = 1.0 / (alpha - beta);
+        }
+        red[NW] = t;
+        red[NW + 1] = beta;
+        red[NW + 2] = scale;
+        red[NW + 3] = vcur[k];
+      }
+    }
+    __syncthreads();
+    const double t = red[NW], scale = red[NW + 2];
+    for (int i = k + 2 + tid; i < n; i += kTrdNT) vcur[i] *= scale;
+    if (tid == 0) vcur[k + 1] = 1.0;
+    __syncthreads();
+    if (r == 0) {
+      for (int i = k + 1 + tid; i < n; i += kTrdNT) Hv[i + L * k] = vcur[i];
+      if (tid == 0) {
+        d[k] = red[NW + 3];
+        e[k] = red[NW + 1];
+        tau[k] = t;
+      }
+    }
+    // owned columns j >= k + 1, two per warp at a time: pending update, then
+    // p_j = tau (A v)_j, and this CTA's share of p . v
+    double* pk = pbuf + (k & 1) * L;
+    const int m0 = (k + 1 > r) ? (k + 1 - r + G - 1) / G : 0;
+    double pv = 0.0;
+    for (int m = m0 + warp;; m += 2 * NW) {
+      const int j1 = r + G * m, j2 = r + G * (m + NW);
+      if (j1 >= n) break;
+      const bool two = j2 < n;
+      const int j2c = two ? j2 : j1;
+      const double vp1 = vprev[j1], wp1 = wprev[j1], vp2 = vprev[j2c], wp2 = wprev[j2c];
+      double q1 = 0.0, q2 = 0.0;
+      double* W1 = W + L * j1;
+      double* W2 = W + L * j2c;
+      int i = k + 1 + lane;
+      // four rows per lane in flight: the column loads are issued before use
+      for (; i + 96 < n; i += 128) {
+        double a1[4], a2[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          a1[u] = W1[i + 32 * u];
+          a2[u] = two ? W2[i + 32 * u] : 0.0;
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int ii = i + 32 * u;
+          const double vi = vprev[ii], wi = wprev[ii], ci = vcur[ii];
+          a1[u] = fma(-wi, vp1, fma(-vi, wp1, a1[u]));
+          q1 = fma(a1[u], ci, q1);
+          if (two) {
+            a2[u] = fma(-wi, vp2, fma(-vi, wp2, a2[u]));
+            q2 = fma(a2[u], ci, q2);
+          }
+        }
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          W1[i + 32 * u] = a1[u];
+          if (two) W2[i + 32 * u] = a2[u];
+        }
+      }
+      for (; i < n; i += 32) {
+        const double vi = vprev[i], wi = wprev[i], ci = vcur[i];
+        const double a1 = fma(-wi, vp1, fma(-vi, wp1, W1[i]));
+        W1[i] = a1;
+        q1 = fma(a1, ci, q1);
+        if (two) {
+          const double a2 = fma(-wi, vp2, fma(-vi, wp2, W2[i]));
+          W2[i] = a2;
+          q2 = fma(a2, ci, q2);
+        }
+        if (k == n - 2) d[n - 1] = a1;  // the last diagonal entry (i = j = n - 1)
+      }
+      q1 = t * warp_sum_xor(q1);
+      q2 = t * warp_sum_xor(q2);
+      if (lane == 0) {
+        pk[j1] = q1;
+        pv = fma(q1, vcur[j1], pv);
+        if (two) {
+          pk[j2] = q2;
+          pv = fma(q2, vcur[j2], pv);
+        }
+      }
+    }
+    if (lane == 0) red[warp] = pv;
+    __syncthreads();
+    double* sdk = sdot + (k & 1) * (L / 2);
+    if (tid == 0) {
+      double sp = 0.0;
+      for (int w = 0; w < NW; ++w) sp += red[w];
+      sdk[r] = sp;
+    }
+    if (G > 1) {
+      if (!trd_group_sync(bar, G * ++nb, s.err, &sh_ok)) return;
+    } else {
+      __syncthreads();
+    }
+    // w = p - (tau / 2) (p . v) v, kept with v for the next step's update
+    if (warp == 0) {
+      double sp = 0.0;
+      for (int c = lane; c < G; c += 32) sp += __ldcg(&sdk[c]);
+      sp = warp_sum_xor(sp);
+      if (lane == 0) red[NW + 4] = 0.5 * t * sp;
+    }
+    for (int i = k + 1 + tid; i < n; i += kTrdNT) wprev[i] = __ldcg(&pk[i]);
+    __syncthreads();
+    const double half = red[NW + 4];
+    for (int i = k + 1 + tid; i < n; i += kTrdNT) {
+      wprev[i] = fma(-half, vcur[i], wprev[i]);
+      vprev[i] = vcur[i];
+    }
+    __syncthreads();
+  }
+}
+
 // The trailing update after panel q: A(k1:, k1:) -= V W^T + W V^T (rows and
 // columns k1.., K = kPnb) on the tensor cores, as two FP64-accurate products
 // whose operand rows are each all reflector entries or all W entries (one
@@ -1287,13 +1469,14 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_finish(Search* S, int s0) {
 // --------------------------------------------------------------------------
 // Host side
 // --------------------------------------------------------------------------
-size_t trd_reduce_smem(int max_n) { return static_cast<size_t>(max_n) * 8; }
+size_t trd_reduce_smem(int max_n, int blocked) { return static_cast<size_t>(max_n) * (blocked ? 8 : 24); }
 
-int trd_reduce_blocks_per_sm(int max_n) {
+int trd_reduce_blocks_per_sm(int max_n, int blocked) {
   int b = 0;
-  const size_t smem = trd_reduce_smem(max_n);
-  cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
-  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, k_trd_panel, kTrdNT, smem) != cudaSuccess) {
+  const size_t smem = trd_reduce_smem(max_n, blocked);
+  const void* fn = blocked ? reinterpret_cast<const void*>(k_trd_panel) : reinterpret_cast<const void*>(k_trd_sytrd);
+  cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, static_cast<int>(smem));
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&b, fn, kTrdNT, smem) != cudaSuccess) {
     cudaGetLastError();
     return 0;
   }
@@ -1302,7 +1485,9 @@ int trd_reduce_blocks_per_sm(int max_n) {
 
 void trd_set_attributes(int max_n) {
   cudaFuncSetAttribute(k_trd_panel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                       static_cast<int>(trd_reduce_smem(max_n)));
+                       static_cast<int>(trd_reduce_smem(max_n, 1)));
+  cudaFuncSetAttribute(k_trd_sytrd, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                       static_cast<int>(trd_reduce_smem(max_n, 0)));
   cudaFuncSetAttribute(k_trd_s2k, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   cudaFuncSetAttribute(k_trd_oz_gram, cudaFuncAttributeMaxDynamicSharedMemorySize, kOzSmem);
   bt_set_attributes();
@@ -1321,11 +1506,11 @@ int launch_eig_trd(Search* S, const int4* grp, const TrdChunk* chunks, int nchun
     if (marks) cudaEventRecord(marks[k], st);
   };
   mark(0);
-  int q_prev = -1;
+  int q_prev = -2;  // chunks of the unblocked form carry panel -1
   for (int c = 0; c < nchunks; ++c) {
     const int q = chunks[c].panel;
     if (q != q_prev) {
-      if (q_prev >= 0 && tm.s2kp.total > 0 && tm.s2k.total > 0) {  // the previous panel's trailing update
+      if (q_prev >= 0 && q >= 0 && tm.s2kp.total > 0 && tm.s2k.total > 0) {  // the previous panel's trailing update
         k_trd_s2k_pack<<<tm.s2kp.total, kOzNT, 0, st>>>(S, tm.s2kp, q_prev);
         k_trd_s2k<<<tm.s2k.total, kOzNT, kOzSmem, st>>>(S, tm.s2k, q_prev);
         nl += 2;
@@ -1334,17 +1519,19 @@ int launch_eig_trd(Search* S, const int4* grp, const TrdChunk* chunks, int nchun
       q_prev = q;
     }
     if (chunks[c].count <= 0) continue;
+    const bool blocked = q >= 0;
     cudaLaunchConfig_t cfg = {};
     cfg.gridDim = dim3(chunks[c].count);
     cfg.blockDim = dim3(kTrdNT);
-    cfg.dynamicSmemBytes = trd_reduce_smem(max_n);
+    cfg.dynamicSmemBytes = trd_reduce_smem(max_n, blocked ? 1 : 0);
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeCooperative;
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
-    cudaLaunchKernelEx(&cfg, k_trd_panel, S, grp + chunks[c].first, q);
+    if (blocked) cudaLaunchKernelEx(&cfg, k_trd_panel, S, grp + chunks[c].first, q);
+    else cudaLaunchKernelEx(&cfg, k_trd_sytrd, S, grp + chunks[c].first);
     ++nl;
   }
   mark(1);
