@@ -782,10 +782,10 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
   CREATE_TRY(cudaMemsetAsync(h->d_err, 0, sizeof(int), h->stream));
   for (int s = 0; s < count; ++s) h->hs[s].err = h->d_err;
   if (h->max_n_trd > 0) {
-    CREATE_TRY(cudaMalloc(&h->d_trd_bar, sizeof(unsigned) * count));
-    CREATE_TRY(cudaMemsetAsync(h->d_trd_bar, 0, sizeof(unsigned) * count, h->stream));
+    CREATE_TRY(cudaMalloc(&h->d_trd_bar, sizeof(unsigned) * count * kTrdBarStride));
+    CREATE_TRY(cudaMemsetAsync(h->d_trd_bar, 0, sizeof(unsigned) * count * kTrdBarStride, h->stream));
     for (int s = 0; s < count; ++s)
-      if (h->hs[s].trd) h->hs[s].trd_bar = h->d_trd_bar + s;
+      if (h->hs[s].trd) h->hs[s].trd_bar = h->d_trd_bar + static_cast<size_t>(s) * kTrdBarStride;
     // groups of the cooperative reduction, within what can be resident at once
     int dev = 0, sms = 0;
     CREATE_TRY(cudaGetDevice(&dev));

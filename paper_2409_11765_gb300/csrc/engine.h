@@ -89,7 +89,7 @@ struct Search {
   int trd, trd_pad_;  // 1: this search's eigendecomposition takes the tridiagonal route
   double* trd_v;      // 11 x ldn doubles: d, e, split e, e^2, tau, eigenvalues (two orders), p and p.v buffers, scalars
   int* trd_i;         // 5 x ldn ints: block start / end, rank, cluster start, V^T V tile flags
-  unsigned* trd_bar;  // the group barrier counter of the reduction
+  unsigned* trd_bar;  // the reduction's counters: group barrier, work per panel step (kTrdBarStride)
   unsigned char* ozp; // packed digit planes of the FP64-accurate tensor-core products (trd_oz_bytes)
   int* oze;           // their row exponents (trd_oz_exps ints)
 };
@@ -244,6 +244,9 @@ int tiles_trd_s2k(int n);       // 128 x 64 tiles of its trailing update
 void trd_set_attributes(int max_n);
 constexpr int kTrdStages = 6;  // reduction, eigenvalues, inverse iteration, clusters, orthogonalisation, back-transformation
 constexpr int kTrdPanel = 64;  // columns per panel of the tridiagonal reduction
+// counters per search of the reduction (Search::trd_bar): the group barrier,
+// then one work counter per step of a panel
+constexpr int kTrdBarStride = 1 + kTrdPanel;
 // One cooperative launch of the reduction: CTAs [first, first + count) of the
 // group table, all working on panel `panel` (-1: the unblocked form, the
 // whole reduction in one launch).

@@ -137,7 +137,7 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
   double* tau = tv(s, TV_TAU);
   double* cbuf = tv(s, TV_P0);
   double* qbuf = tv(s, TV_P1);
-  double* pvp = tv(s, TV_SD);         // per-CTA partial q . v
+  double* qv = tv(s, TV_SD);          // q(j) v(j) per column
   double* ubuf = s.EH;                // u_W (kPnb), u_V (kPnb)
   double* part = s.EH + kUbuf;        // per-CTA partial |c|^2, kPartStride apart
   unsigned* bar = s.trd_bar;
@@ -173,7 +173,7 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
       __syncthreads();
       if (warp == 0) {  // q . v, u_W . u_V and the row-k correction, lanes in fixed order
         double sq = 0.0, uu = 0.0, ck = 0.0;
-        for (int c = lane; c < G; c += 32) sq += __ldcg(&pvp[c]);
+        for (int c = k + lane; c < n; c += 32) sq += __ldcg(&qv[c]);
         for (int l = lane; l < jp; l += 32) {
           uu = fma(su[l], su[kPnb + l], uu);
           ck = fma(sVk[l], su[l], fma(sWk[l], su[kPnb + l], ck));
@@ -292,48 +292,57 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
       const int i = 32 * c + lane;
       if (i > k && i < n) Hv[i + L * k] = vsm[i];
     }
-    // own columns j' >= k + 1 of A, two per warp at a time, then the own
-    // columns of [W V] (index j + l' ... over the 2j of them, l' mod G = r)
-    const int m0 = (k + 1 > r) ? (k + 1 - r + G - 1) / G : 0;
-    double pv = 0.0;
-    for (int m = m0 + warp;; m += 2 * NW) {
-      const int j1 = r + G * m, j2 = r + G * (m + NW);
-      if (j1 >= n) break;
-      const bool two = j2 < n;
-      const int j2c = two ? j2 : j1;
-      const double* A1 = A + L * j1;
-      const double* A2 = A + L * j2c;
-      double q1 = 0.0, q2 = 0.0;
-      int i = k + 1 + lane;
-      constexpr int U = 8;  // rows per lane in flight, two columns
-      for (; i + 32 * (U - 1) < n; i += 32 * U) {
-        double a1[U], a2[U];
+    // columns j' >= k + 1 of A two at a time, dealt at run time to the
+    // group's warps from the step's work counter (the next pair is claimed
+    // before the current one is worked); then the own columns of [W V]
+    // (index x over the 2j of them, x mod G = r)
+    {
+      unsigned* wctr = bar + 1 + j;
+      const int units = (n - k) >> 1;  // pairs (k+1, k+2), (k+3, k+4), ...; the last may be single
+      int u = 0;
+      if (lane == 0) u = static_cast<int>(atomicAdd(wctr, 1u));
+      u = __shfl_sync(0xffffffffu, u, 0);
+      while (u < units) {
+        int un = 0;
+        if (lane == 0) un = static_cast<int>(atomicAdd(wctr, 1u));
+        const int j1 = k + 1 + 2 * u, j2 = j1 + 1;
+        const bool two = j2 < n;
+        const int j2c = two ? j2 : j1;
+        const double* A1 = A + L * j1;
+        const double* A2 = A + L * j2c;
+        double q1 = 0.0, q2 = 0.0;
+        int i = k + 1 + lane;
+        constexpr int U = 8;  // rows per lane in flight, two columns
+        for (; i + 32 * (U - 1) < n; i += 32 * U) {
+          double a1[U], a2[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          a1[u] = A1[i + 32 * u];
-          a2[u] = two ? A2[i + 32 * u] : 0.0;
-        }
+          for (int uu = 0; uu < U; ++uu) {
+            a1[uu] = __ldcg(&A1[i + 32 * uu]);
+            a2[uu] = two ? __ldcg(&A2[i + 32 * uu]) : 0.0;
+          }
 #pragma unroll
-        for (int u = 0; u < U; ++u) {
-          const double vi = vsm[i + 32 * u];
-          q1 = fma(a1[u], vi, q1);
-          q2 = fma(a2[u], vi, q2);
+          for (int uu = 0; uu < U; ++uu) {
+            const double vi = vsm[i + 32 * uu];
+            q1 = fma(a1[uu], vi, q1);
+            q2 = fma(a2[uu], vi, q2);
+          }
         }
-      }
-      for (; i < n; i += 32) {
-        const double vi = vsm[i];
-        q1 = fma(A1[i], vi, q1);
-        if (two) q2 = fma(A2[i], vi, q2);
-      }
-      q1 = warp_sum_xor(q1);
-      q2 = warp_sum_xor(q2);
-      if (lane == 0) {
-        qbuf[j1] = q1;
-        pv = fma(q1, vsm[j1], pv);
-        if (two) {
-          qbuf[j2] = q2;
-          pv = fma(q2, vsm[j2], pv);
+        for (; i < n; i += 32) {
+          const double vi = vsm[i];
+          q1 = fma(__ldcg(&A1[i]), vi, q1);
+          if (two) q2 = fma(__ldcg(&A2[i]), vi, q2);
         }
+        q1 = warp_sum_xor(q1);
+        q2 = warp_sum_xor(q2);
+        if (lane == 0) {
+          qbuf[j1] = q1;
+          qv[j1] = q1 * vsm[j1];
+          if (two) {
+            qbuf[j2] = q2;
+            qv[j2] = q2 * vsm[j2];
+          }
+        }
+        u = __shfl_sync(0xffffffffu, un, 0);
       }
     }
     for (int x = r + G * warp; x < 2 * j; x += G * NW) {  // u = [W V]^T v over rows k+1..
@@ -342,13 +351,6 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
       for (int i = k + 1 + lane; i < n; i += 32) acc = fma(__ldcg(&col[i]), vsm[i], acc);
       acc = warp_sum_xor(acc);
       if (lane == 0) ubuf[x < j ? x : kPnb + x - j] = acc;
-    }
-    if (lane == 0) red[warp] = pv;
-    __syncthreads();
-    if (tid == 0) {
-      double sp = 0.0;
-      for (int w = 0; w < NW; ++w) sp += red[w];
-      pvp[r] = sp;
     }
     if (!barrier(mbase + 2u * j + 2u)) return;
     tprev = t;
@@ -1515,7 +1517,8 @@ int launch_eig_trd(Search* S, const int4* grp, const TrdChunk* chunks, int nchun
         k_trd_s2k<<<tm.s2k.total, kOzNT, kOzSmem, st>>>(S, tm.s2k, q_prev);
         nl += 2;
       }
-      cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count, st);  // the group barriers restart per panel
+      // the group barriers and work counters restart per panel
+      cudaMemsetAsync(bars, 0, sizeof(unsigned) * bar_count * kTrdBarStride, st);
       q_prev = q;
     }
     if (chunks[c].count <= 0) continue;
