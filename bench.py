@@ -230,11 +230,20 @@ class ClockSampler:
 PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
 
-# DRAM bytes per launch of the dominant kernel from one ncu capture, valid only
+# DRAM bytes per step of the dominant stage from one ncu capture, valid only
 # for the engine sources it was measured on (a SHA-256 of the CUDA sources
 # without comments): after any change to them the roofline's traffic is null
-# until it is measured again. Empty until a capture of the current sources.
-KERNEL_TRAFFIC = {}
+# until it is measured again.
+#   reduction: dram__bytes_read.sum + dram__bytes_write.sum of k_trd_panel,
+#   k_trd_s2k_pack and k_trd_s2k over four generations of the first 32
+#   searches of the 256-search batch (22.96 GB, 5.74 GB per generation),
+#   scaled to the full batch by the sum of n^3 over the decompositions a step
+#   does (367.2e9 / 17.35e9 = 21.2). The full batch keeps more matrices in
+#   flight than L2 holds, so this is a lower bound on its traffic.
+KERNEL_TRAFFIC = {
+    "reduction": {"bytes_per_step": 5.739e9 * 21.16, "sources_sha256_16": "0f83423a4fb2d80b",
+                  "capture": "batch256-first32, 4 generations, scaled by sum n^3"},
+}
 
 
 def engine_sources_sha():
