@@ -83,6 +83,8 @@ typedef enum {
 #define CMAES_STOP_FTARGET 1        /* best f < f_target: the search ends      */
 #define CMAES_STOP_MAXITER 2        /* generations >= max_iter                 */
 #define CMAES_STOP_TOLHISTFUN 4     /* range of recent best f < tol_hist_fun   */
+                                    /* (mixed handles: or < 10 x the largest   */
+                                    /* |f_mixed - f_FP64| of those best points) */
 #define CMAES_STOP_TOLX 8           /* sigma * max(|p_c|, sqrt(diag C)) < tolx */
 #define CMAES_STOP_CONDITIONCOV 16  /* cond(C) > cond_max                      */
 #define CMAES_STOP_NOEFFECTAXIS 32  /* 0.1 sigma D_j b_j does not move m       */

@@ -643,7 +643,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     size_t b = 0;
     b += 9 * align256(ldn * 8);                       // vectors
     b += align256(static_cast<size_t>(x.mu_cap) * 8);  // w
-    b += align256(static_cast<size_t>(x.hist_cap) * 8);
+    b += align256(static_cast<size_t>(2 * x.hist_cap) * 8);  // best f, then its mixed-evaluation error
     b += align256(static_cast<size_t>(part_doubles(n, x.ldn, x.mu_cap)) * 8);
     if (h->mixed) {
       b += align256(static_cast<size_t>(tiles_tc_sym(n)) * x.covm_nch * 16384 * 8);
@@ -722,7 +722,7 @@ cmaes_status cmaes_create_batch(int count, const int* n_arr, const int* lam_arr,
     x.yw = reinterpret_cast<double*>(take(ldn * 8));
     x.zw = reinterpret_cast<double*>(take(ldn * 8));
     x.w = reinterpret_cast<double*>(take(static_cast<size_t>(x.mu_cap) * 8));
-    x.hist = reinterpret_cast<double*>(take(static_cast<size_t>(x.hist_cap) * 8));
+    x.hist = reinterpret_cast<double*>(take(static_cast<size_t>(2 * x.hist_cap) * 8));
     x.part = reinterpret_cast<double*>(take(static_cast<size_t>(part_doubles(x.n, x.ldn, x.mu_cap)) * 8));
     const size_t kp = x.kp;
     if (h->mixed) {
@@ -1245,6 +1245,8 @@ cmaes_status cmaes_set_state(cmaes_t h, int s, const cmaes_state* st) {
   cur.eig_due = 0;
   const int keep = st->hist_count < hist_len ? st->hist_count : hist_len;
   cur.hist_count = keep;
+  // the snapshot holds no evaluation errors: a restored window counts them as 0
+  CUDA_TRY(h, cudaMemset(x.hist + x.hist_cap, 0, static_cast<size_t>(x.hist_cap) * 8));
   if (keep > 0) {
     CUDA_TRY(h, cudaMemcpy(x.hist, st->hist + (st->hist_count - keep), static_cast<size_t>(keep) * 8,
                            cudaMemcpyHostToDevice));

@@ -35,6 +35,11 @@ struct DevOptions {
   uint32_t key0, key1;  // Philox key (seed)
 };
 
+// TolHistFun on a mixed handle: the window's range of best f is compared with
+// at least this multiple of the largest |f_mixed - f_FP64| of its best points
+// (Search::hist holds the best values, then those errors, hist_cap apart).
+constexpr double kMixedResolution = 10.0;
+
 // Per-search descriptor, resident in device memory. Constant part first,
 // then the scalars that the kernels update every generation.
 // Bits of the device status word (Search::err): a bounded device wait gave up

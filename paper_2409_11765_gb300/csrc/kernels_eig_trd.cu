@@ -22,7 +22,8 @@
 //      with partial pivoting on T - lambda I, three solves from a
 //      pseudo-random start); vectors of one block whose eigenvalues lie within
 //      1e-13 ||T|| of each other (where inverse iteration may return nearly
-//      parallel vectors) are orthogonalised by modified Gram-Schmidt (twice),
+//      parallel vectors) are orthogonalised by Gram-Schmidt (twice; classical
+//      on a whole CTA for long chunks, modified on one warp for short ones),
 //      in chunks of at most 64 consecutive vectors: a longer chain is a
 //      repeated eigenvalue spread by rounding, whose vectors come from
 //      independent pseudo-random starts and overlap little across chunks.
@@ -332,15 +333,18 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
           q1 = fma(__ldcg(&A1[i]), vi, q1);
           if (two) q2 = fma(__ldcg(&A2[i]), vi, q2);
         }
-        q1 = warp_sum_xor(q1);
-        q2 = warp_sum_xor(q2);
+        // both sums in one tree: the first level leaves column 1's pairs on
+        // lanes 0-15 and column 2's on lanes 16-31 (five FP64 adds, not ten)
+        const bool hi = (lane & 16) != 0;
+        double qs = (hi ? q2 : q1) + __shfl_xor_sync(0xffffffffu, hi ? q1 : q2, 16);
+#pragma unroll
+        for (int o = 8; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
         if (lane == 0) {
-          qbuf[j1] = q1;
-          qv[j1] = q1 * vsm[j1];
-          if (two) {
-            qbuf[j2] = q2;
-            qv[j2] = q2 * vsm[j2];
-          }
+          qbuf[j1] = qs;
+          qv[j1] = qs * vsm[j1];
+        } else if (lane == 16 && two) {
+          qbuf[j2] = qs;
+          qv[j2] = qs * vsm[j2];
         }
         u = __shfl_sync(0xffffffffu, un, 0);
       }
@@ -1054,8 +1058,15 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_invit(Search* S, TileMap tm) {
 }
 
 // --------------------------------------------------------------------------
-// 4c. Modified Gram-Schmidt (twice) inside each cluster of close eigenvalues
-// of one block; one warp per cluster chunk, 16 CTAs per search.
+// 4c. Gram-Schmidt (twice) inside each cluster of close eigenvalues of one
+// block, in chunks of at most kTrdClusMax consecutive vectors (independent of
+// one another). A long chunk on a long block goes to a whole CTA as classical
+// Gram-Schmidt applied twice (all projections of a vector at once: the dots
+// spread over the warps, the update over the rows, the vector in shared
+// memory); a short one to one warp as modified Gram-Schmidt, twice. Both keep
+// the orthogonality that the later Newton-Schulz steps need (Giraud, Langou &
+// Rozloznik 2005: two passes of either are enough for vectors that are not
+// numerically dependent).
 // --------------------------------------------------------------------------
 // Modified Gram-Schmidt, twice, on vectors [c, ce) of rows [r0, r1) (one warp).
 __device__ void cluster_mgs(double* V, long long L, int c, int ce, int r0, int r1, int lane) {
@@ -1086,9 +1097,72 @@ __device__ void cluster_mgs(double* V, long long L, int c, int ce, int r0, int r
   }
 }
 
-constexpr int kTrdMgsCtas = 16;  // CTAs per search of the Gram-Schmidt kernel
+// Classical Gram-Schmidt, twice, on vectors [c, ce) of rows [r0, r1) (the
+// whole CTA; r1 - r0 <= kEigBigMaxN). Per vector a and pass: p = V_prev^T v_a
+// (warp w takes the previous vectors w, w + 8, ...), then v_a -= V_prev p on
+// every row (the terms in ascending order); then v_a / |v_a|.
+__device__ void cluster_cgs2_cta(double* V, long long L, int c, int ce, int r0, int r1, double* va,
+                                 double* pb, double* red) {
+  constexpr int NW = kTrdNT / 32;
+  const int R = r1 - r0, tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  for (int a = c; a < ce; ++a) {
+    double* col = V + L * a + r0;
+    for (int i = tid; i < R; i += kTrdNT) va[i] = col[i];
+    __syncthreads();
+    const int m = a - c;
+    for (int rep = 0; rep < (m > 0 ? 2 : 0); ++rep) {
+      for (int x = warp; x < m; x += NW) {
+        const double* vb = V + L * (c + x) + r0;
+        double p0 = 0.0, p1 = 0.0, p2 = 0.0, p3 = 0.0;
+        int i = lane;
+        for (; i + 96 < R; i += 128) {  // four rows per lane in flight
+          p0 = fma(vb[i], va[i], p0);
+          p1 = fma(vb[i + 32], va[i + 32], p1);
+          p2 = fma(vb[i + 64], va[i + 64], p2);
+          p3 = fma(vb[i + 96], va[i + 96], p3);
+        }
+        for (; i < R; i += 32) p0 = fma(vb[i], va[i], p0);
+        const double p = warp_sum_xor((p0 + p1) + (p2 + p3));
+        if (lane == 0) pb[x] = p;
+      }
+      __syncthreads();
+      for (int i = tid; i < R; i += kTrdNT) {
+        const double* vb = V + L * c + r0 + i;
+        double acc = va[i];
+        int x = 0;
+        for (; x + 4 <= m; x += 4) {
+          const double b0 = vb[L * x], b1 = vb[L * (x + 1)], b2 = vb[L * (x + 2)], b3 = vb[L * (x + 3)];
+          acc = fma(-pb[x], b0, acc);
+          acc = fma(-pb[x + 1], b1, acc);
+          acc = fma(-pb[x + 2], b2, acc);
+          acc = fma(-pb[x + 3], b3, acc);
+        }
+        for (; x < m; ++x) acc = fma(-pb[x], vb[L * x], acc);
+        va[i] = acc;
+      }
+      __syncthreads();
+    }
+    double q = 0.0;
+    for (int i = tid; i < R; i += kTrdNT) q = fma(va[i], va[i], q);
+    q = warp_sum_xor(q);
+    if (lane == 0) red[warp] = q;
+    __syncthreads();
+    double nq = 0.0;
+    for (int w = 0; w < NW; ++w) nq += red[w];
+    const double inv = 1.0 / sqrt(nq);
+    for (int i = tid; i < R; i += kTrdNT) col[i] = va[i] * inv;
+    __syncthreads();  // v_a complete before the next vector reads it (and red is reused)
+  }
+}
+
+constexpr int kTrdMgsCtas = 32;    // CTAs per search of the Gram-Schmidt kernel
+constexpr int kTrdCgsMinVec = 8;   // chunks of at least this many vectors
+constexpr int kTrdCgsMinRows = 256;  // on blocks of at least this many rows go to a CTA
 
 __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
+  __shared__ double va[kEigBigMaxN];
+  __shared__ double pb[kTrdClusMax];
+  __shared__ double red[kTrdNT / 32];
   Search& s = S[s0 + blockIdx.x];
   if (!trd_due(s)) return;
   const int n = s.n, lane = threadIdx.x & 31;
@@ -1098,16 +1172,27 @@ __global__ void __launch_bounds__(kTrdNT) k_trd_mgs(Search* S, int s0) {
   const int* b0a = ti(s, TI_B0);
   const int* b1a = ti(s, TI_B1);
   double* V = s.ET;
-  // work items: the chunks of at most kTrdClusMax vectors of every cluster of
-  // two or more (independent of one another), dealt round-robin to the warps
-  int found = 0;
-  for (int c = 0; c < n; ++c) {
-    if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;
-    int ce = c + 1;
-    while (ce < n && cl0[ce] == c) ++ce;
-    for (int cc = c; cc < ce; cc += kTrdClusMax)
-      if ((found++ % (kTrdMgsCtas * kTrdNT / 32)) == warp)
-        cluster_mgs(V, L, cc, min(ce, cc + kTrdClusMax), b0a[c], b1a[c], lane);
+  // work items: the chunks of every cluster of two or more; the long ones
+  // dealt round-robin to the CTAs (pass 0), the others to the warps (pass 1)
+  for (int pass = 0; pass < 2; ++pass) {
+    int found = 0;
+    for (int c = 0; c < n; ++c) {
+      if (cl0[c] != c || c + 1 >= n || cl0[c + 1] != c) continue;
+      int ce = c + 1;
+      while (ce < n && cl0[ce] == c) ++ce;
+      const int r0 = b0a[c], r1 = b1a[c];
+      for (int cc = c; cc < ce; cc += kTrdClusMax) {
+        const int cn = min(ce, cc + kTrdClusMax);
+        const bool big = cn - cc >= kTrdCgsMinVec && r1 - r0 >= kTrdCgsMinRows;
+        if (big != (pass == 0)) continue;
+        if (big) {
+          if ((found++ % kTrdMgsCtas) == static_cast<int>(blockIdx.y))
+            cluster_cgs2_cta(V, L, cc, cn, r0, r1, va, pb, red);
+        } else if ((found++ % (kTrdMgsCtas * kTrdNT / 32)) == warp) {
+          cluster_mgs(V, L, cc, cn, r0, r1, lane);
+        }
+      }
+    }
   }
 }
 

@@ -494,11 +494,14 @@ __global__ void __launch_bounds__(256) k_finalize(Search* S, int s0) {
   }
   const int i0 = s.order[0];
   double f0 = s.f[i0];
+  double ferr = 0.0;
   if (s.mixed && s.obj != 0) {
-    // the value that decides the best point and the history is the FP64 one
+    // the value that decides the best point and the history is the FP64 one;
+    // its distance from the mixed value that ranked it is kept beside it
     double acc = 0.0;
     for (int t = 0; t < tiles_reeval(n); ++t) acc += s.fpart[t];
     f0 = (s.obj == 2) ? 10.0 * n + acc : acc;
+    ferr = fabs(s.f[i0] - f0);
   }
   const bool better = f0 < s.best_f;
   if (better) {
@@ -512,6 +515,7 @@ __global__ void __launch_bounds__(256) k_finalize(Search* S, int s0) {
     s.sigma = sigma * exp((s.cs / s.ds) * (psn / s.chin - 1.0));
     if (better) s.best_f = f0;
     s.hist[s.hist_count % s.hist_len] = f0;
+    s.hist[s.hist_cap + s.hist_count % s.hist_len] = ferr;
     s.hist_count += 1;
     s.gen += 1;
     s.eig_due = (s.gen % s.g_eig) == 0;
@@ -685,12 +689,17 @@ __global__ void __launch_bounds__(256) k_stop(Search* S, int s0, DevOptions o) {
     if (s.best_f < o.f_target) flags |= 1;
     if (s.gen >= s.max_iter) flags |= 2;
     if (s.hist_count >= s.hist_len) {
-      double hmax = -INFINITY, hmin = INFINITY;
+      // TolHistFun; on a mixed handle the range is compared with at least
+      // kMixedResolution times the largest mixed-evaluation error of the
+      // window's best values (below that the mixed ranking cannot tell the
+      // candidates apart, so the descent cannot make further progress)
+      double hmax = -INFINITY, hmin = INFINITY, emax = 0.0;
       for (int q = 0; q < s.hist_len; ++q) {
         hmax = fmax(hmax, s.hist[q]);
         hmin = fmin(hmin, s.hist[q]);
+        emax = fmax(emax, s.hist[s.hist_cap + q]);
       }
-      if (hmax - hmin < o.tol_hist_fun) flags |= 4;
+      if (hmax - hmin < fmax(o.tol_hist_fun, kMixedResolution * emax)) flags |= 4;
     }
     if (!any_tolx_fail) flags |= 8;
     if (__dmul_rn(dmax, dmax) > __dmul_rn(__dmul_rn(o.cond_max, dmin), dmin)) flags |= 16;

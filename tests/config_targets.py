@@ -22,7 +22,8 @@ reports how far it got.
 The best point of every search that reports a reached target is re-evaluated
 in FP64 by the oracle's objective, so a mixed-precision hit is a true hit.
 
-    python tests/config_targets.py [--only LABEL-SUBSTRING] [--json out.json]
+    python tests/config_targets.py [--only LABEL-SUBSTRING] [--precision fp64|tf32]
+                                   [--json out.json]
 """
 import argparse
 import json
@@ -129,6 +130,7 @@ def fp64_recheck(wl, best):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="")
+    ap.add_argument("--precision", choices=["fp64", "tf32"], default=None)
     ap.add_argument("--json", default="")
     ap.add_argument("--seed", type=int, default=20240918)
     args = ap.parse_args()
@@ -140,6 +142,8 @@ def main():
         if args.only and args.only not in label:
             continue
         for pname, prec in PRECISIONS:
+            if args.precision and pname != args.precision:
+                continue
             c = counting_run(eng, wl, prec, args.seed, max_gens, max_s)
             gens = c["hit_gen"] if c["hit_gen"] is not None else c["gens"]
             cand = c["hit_cand"] if c["hit_cand"] is not None else c["cand"]

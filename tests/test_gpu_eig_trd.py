@@ -57,11 +57,13 @@ def test_route_matches_oracle(method, n, lam, kind, cond):
 
 
 @pytest.mark.parametrize("method", [2])
-@pytest.mark.parametrize("n,lam", [(40, 12), (200, 24), (600, 30)])
+@pytest.mark.parametrize("n,lam", [(40, 12), (200, 24), (600, 30), (1000, 12), (2000, 26)])
 def test_first_generation_repeated_eigenvalue(method, n, lam):
     """From C = I with lambda < n: C' = a I + a rank-(mu + 1) update, whose
     eigenvalue a repeats n - mu - 1 times (any basis of that eigenspace is
-    correct; the checks skip eigenvectors of repeated eigenvalues). The
+    correct; the checks skip eigenvectors of repeated eigenvalues). At
+    n = 1000 and 2000 the repeated eigenvalue's chain of inverse-iteration
+    vectors is long enough for the CTA-wide Gram-Schmidt chunks. The
     warm-started Jacobi route is not run here: on this spectrum its FP32 stage
     and cleanup leave eigenvalue errors of ~3e-11 of the largest at n = 200."""
     d = _fresh(n, 1200 + n)

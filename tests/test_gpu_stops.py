@@ -268,3 +268,39 @@ def test_injected_device_timeout_is_sticky():
         assert "timed out" in eng.cmaes_last_error(h)
     finally:
         eng.cmaes_destroy(h)
+
+
+def test_mixed_descent_stalled_at_its_resolution_restarts():
+    """A mixed (TF32) descent that settles in a local minimum of the rotated
+    Rastrigin (n = 100, lambda = 17, the sequential IPOP start) ranks its
+    candidates by values whose error (~1e-6 of f, the FP32 epilogue) exceeds
+    their differences, so its FP64 best values keep moving by more than the
+    absolute TolHistFun tolerance; TolHistFun then compares the window's range
+    with 10 x the window's largest |f_mixed - f_FP64| of those best points, and
+    the descent restarts within 20,000 generations, as on the FP64 path (before
+    that rule it ran on towards MaxIter, ~128,000 generations)."""
+    import paper_2409_11765_gb300 as eng
+    from paper_2409_11765_gb300 import workloads as W
+    wl = W.rastrigin_n100_ipop(concurrent=False)
+    s = wl.searches[0]
+    res = {}
+    for prec in (0, 1):
+        opt = eng.cmaes_default_options(precision=prec, f_target=wl.f_target, box_lo=wl.box_lo,
+                                        box_hi=wl.box_hi, max_restarts=1, ipop_double=1)
+        h = eng.cmaes_create(s.n, s.lam, s.x0, s.sigma0, SEED, opt)
+        try:
+            p = s.problem
+            eng.cmaes_set_problem(h, 0, p.kind, p.Q, p.lamdiag, p.xstar)
+            gens = 0
+            while gens < 20000:
+                eng.cmaes_step_batch(h, 250)
+                gens += 250
+                q = eng.cmaes_query(h, 0)
+                if q["restart"] >= 1 or q["done"]:
+                    break
+            res[prec] = (gens, q)
+        finally:
+            eng.cmaes_destroy(h)
+    for prec, (gens, q) in res.items():
+        assert q["restart"] >= 1 or q["done"], (prec, gens, q)
+        assert q["lam"] == 34 or q["done"], (prec, q)
