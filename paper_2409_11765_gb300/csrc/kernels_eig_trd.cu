@@ -94,8 +94,9 @@ __device__ bool trd_group_sync(unsigned* ctr, unsigned target, int* err, int* sh
 // by step; after the panel the trailing part of A takes that rank-2 kPnb
 // update as FP64-accurate products on the tensor cores (k_trd_s2k_*).
 // CTA blockIdx.x works for search grp[b].x as member r = grp[b].y of a group
-// of G = grp[b].z CTAs: it owns the columns j with j mod G = r and the 32-row
-// chunks c with c mod G = r. Step k (panel column j = k - k0) in two phases:
+// of G = grp[b].z CTAs: it owns the 32-row chunks c with c mod G = r (the
+// column products are dealt at run time). Step k (panel column j = k - k0) in
+// two phases:
 //   A. with u_W = W^T v, u_V = V^T v (the previous step's v, from the previous
 //      phase B) and q = A v on the own rows, the previous step's
 //      p = tau (q - V u_W - W u_V) and w = p - (tau / 2)(p . v) v, where
@@ -103,9 +104,11 @@ __device__ bool trd_group_sync(unsigned* ctr, unsigned target, int* err, int* sh
 //      rows, column k of the current matrix, c = A(:, k) - V W(k, :)^T -
 //      W V(k, :)^T (to cbuf), and the partial sum of |c(k+2:)|^2;
 //                                                               group barrier
-//   B. (every CTA) the reflector of c and its vector v; on the own columns
-//      q(j') = A(:, j')^T v (to qbuf) and the partial q . v; on the own
-//      columns of [W V] (2j of them), u = [W V]^T v over rows k+1..;
+//   B. (every CTA) the reflector of c and its vector v; then the products
+//      q(j') = A(:, j')^T v (to qbuf, and q(j') v(j') to qv) and
+//      u = [W V]^T v over rows k+1.., column pairs dealt to the group's warps
+//      from a per-step counter; q . v is summed in phase A of the next step
+//      over all rows by all warps, in a fixed order;
 //                                                               group barrier
 // The group (its size may differ from panel to panel) counts its barriers
 // from the start of the panel: barrier m waits for G m arrivals; in panel 0
@@ -171,18 +174,29 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
         sVk[l] = __ldcg(&Hv[k + L * (k0 + l)]);
         sWk[l] = __ldcg(&Wp[k + L * l]);
       }
+      {  // q . v: warp w sums rows k + 32 w + lane + 256 m (two chains), in fixed order
+        double s0 = 0.0, s1 = 0.0;
+        int c = k + 32 * warp + lane;
+        for (; c + kTrdNT < n; c += 2 * kTrdNT) {
+          s0 += __ldcg(&qv[c]);
+          s1 += __ldcg(&qv[c + kTrdNT]);
+        }
+        if (c < n) s0 += __ldcg(&qv[c]);
+        const double sw = warp_sum_xor(s0 + s1);
+        if (lane == 0) red[warp] = sw;
+      }
       __syncthreads();
-      if (warp == 0) {  // q . v, u_W . u_V and the row-k correction, lanes in fixed order
-        double sq = 0.0, uu = 0.0, ck = 0.0;
-        for (int c = k + lane; c < n; c += 32) sq += __ldcg(&qv[c]);
+      if (warp == 0) {  // u_W . u_V and the row-k correction, lanes in fixed order
+        double uu = 0.0, ck = 0.0;
         for (int l = lane; l < jp; l += 32) {
           uu = fma(su[l], su[kPnb + l], uu);
           ck = fma(sVk[l], su[l], fma(sWk[l], su[kPnb + l], ck));
         }
-        sq = warp_sum_xor(sq);
         uu = warp_sum_xor(uu);
         ck = warp_sum_xor(ck);
         if (lane == 0) {
+          double sq = 0.0;
+          for (int w = 0; w < NW; ++w) sq += red[w];
           const double half = 0.5 * tprev * tprev * (sq - 2.0 * uu);  // (tau / 2) p . v
           const double pk = tprev * (__ldcg(&qbuf[k]) - ck);
           sVk[jp] = 1.0;                // v_{k-1}(k)
@@ -197,8 +211,9 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
     for (int c = first_chunk(k) + G * warp; 32 * c < n; c += G * NW) {
       const int i = 32 * c + lane;
       if (i < k || i >= n) continue;
-      double pc = 0.0;  // V u_W + W u_V (previous step), then the column correction
-      double cc = 0.0;
+      // V u_W + W u_V (previous step), then the column correction: two
+      // chains each (even and odd columns of every group of eight), summed last
+      double pc0 = 0.0, pc1 = 0.0, cc0 = 0.0, cc1 = 0.0;
       int l = 0;
       for (; l + 8 <= jp; l += 8) {  // eight columns' loads in flight
         double hv[8], wv[8];
@@ -208,16 +223,20 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
           wv[u] = __ldcg(&Wp[i + L * (l + u)]);
         }
 #pragma unroll
-        for (int u = 0; u < 8; ++u) {
-          pc = fma(hv[u], su[l + u], fma(wv[u], su[kPnb + l + u], pc));
-          cc = fma(hv[u], sWk[l + u], fma(wv[u], sVk[l + u], cc));
+        for (int u = 0; u < 8; u += 2) {
+          pc0 = fma(hv[u], su[l + u], fma(wv[u], su[kPnb + l + u], pc0));
+          cc0 = fma(hv[u], sWk[l + u], fma(wv[u], sVk[l + u], cc0));
+          pc1 = fma(hv[u + 1], su[l + u + 1], fma(wv[u + 1], su[kPnb + l + u + 1], pc1));
+          cc1 = fma(hv[u + 1], sWk[l + u + 1], fma(wv[u + 1], sVk[l + u + 1], cc1));
         }
       }
       for (; l < jp; ++l) {
         const double hv = __ldcg(&Hv[i + L * (k0 + l)]), wv = __ldcg(&Wp[i + L * l]);
-        pc = fma(hv, su[l], fma(wv, su[kPnb + l], pc));
-        cc = fma(hv, sWk[l], fma(wv, sVk[l], cc));
+        pc0 = fma(hv, su[l], fma(wv, su[kPnb + l], pc0));
+        cc0 = fma(hv, sWk[l], fma(wv, sVk[l], cc0));
       }
+      const double pc = pc0 + pc1;
+      double cc = cc0 + cc1;
       if (j > 0) {
         const double vi = vsm[i];  // v_{k-1}(i)
         const double wi = fma(-half, vi, tprev * (__ldcg(&qbuf[i]) - pc));
@@ -261,10 +280,11 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
       a = warp_sum_xor(a);
       if (lane == 0) red[NW + 1] = a;
     }
-    if (tid == 32) {  // the diagonal entry of column k
-      double acc = __ldcg(&A[k + L * k]);
-      for (int l = 0; l < j; ++l) acc = fma(-2.0 * sVk[l], sWk[l], acc);
-      red[NW + 2] = acc;
+    if (warp == 1) {  // the diagonal entry of column k: A(k, k) - 2 V(k, :) W(k, :)^T
+      double acc = 0.0;
+      for (int l = lane; l < j; l += 32) acc = fma(sVk[l], sWk[l], acc);
+      acc = warp_sum_xor(acc);
+      if (lane == 0) red[NW + 2] = fma(-2.0, acc, __ldcg(&A[k + L * k]));
     }
     if (tid == 64) red[NW + 5] = __ldcg(&cbuf[k + 1]);  // alpha
     __syncthreads();
@@ -293,24 +313,36 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
       const int i = 32 * c + lane;
       if (i > k && i < n) Hv[i + L * k] = vsm[i];
     }
-    // columns j' >= k + 1 of A two at a time, dealt at run time to the
+    // columns j' >= k + 1 of A two at a time, then the 2j columns of [W V]
+    // two at a time (u = [W V]^T v over rows k+1..), dealt at run time to the
     // group's warps from the step's work counter (the next pair is claimed
-    // before the current one is worked); then the own columns of [W V]
-    // (index x over the 2j of them, x mod G = r)
+    // before the current one is worked)
     {
       unsigned* wctr = bar + 1 + j;
-      const int units = (n - k) >> 1;  // pairs (k+1, k+2), (k+3, k+4), ...; the last may be single
+      const int units_a = (n - k) >> 1;  // pairs (k+1, k+2), (k+3, k+4), ...; the last may be single
+      const int units = units_a + j;
       int u = 0;
       if (lane == 0) u = static_cast<int>(atomicAdd(wctr, 1u));
       u = __shfl_sync(0xffffffffu, u, 0);
       while (u < units) {
         int un = 0;
         if (lane == 0) un = static_cast<int>(atomicAdd(wctr, 1u));
-        const int j1 = k + 1 + 2 * u, j2 = j1 + 1;
-        const bool two = j2 < n;
-        const int j2c = two ? j2 : j1;
-        const double* A1 = A + L * j1;
-        const double* A2 = A + L * j2c;
+        const bool is_a = u < units_a;
+        int j1, j2;            // A: columns j1, j2; [W V]: entries j1, j2 of the 2j
+        const double *A1, *A2;
+        bool two = true;
+        if (is_a) {
+          j1 = k + 1 + 2 * u;
+          j2 = j1 + 1;
+          two = j2 < n;
+          A1 = A + L * j1;
+          A2 = A + L * (two ? j2 : j1);
+        } else {
+          j1 = 2 * (u - units_a);
+          j2 = j1 + 1;
+          A1 = j1 < j ? Wp + L * j1 : Hv + L * (k0 + j1 - j);
+          A2 = j2 < j ? Wp + L * j2 : Hv + L * (k0 + j2 - j);
+        }
         double q1 = 0.0, q2 = 0.0;
         int i = k + 1 + lane;
         constexpr int U = 8;  // rows per lane in flight, two columns
@@ -339,22 +371,15 @@ __global__ void __launch_bounds__(kTrdNT, 4) k_trd_panel(Search* S, const int4* 
         double qs = (hi ? q2 : q1) + __shfl_xor_sync(0xffffffffu, hi ? q1 : q2, 16);
 #pragma unroll
         for (int o = 8; o > 0; o >>= 1) qs += __shfl_xor_sync(0xffffffffu, qs, o);
-        if (lane == 0) {
-          qbuf[j1] = qs;
-          qv[j1] = qs * vsm[j1];
-        } else if (lane == 16 && two) {
-          qbuf[j2] = qs;
-          qv[j2] = qs * vsm[j2];
+        const int jw = lane == 0 ? j1 : j2;
+        if ((lane == 0 || (lane == 16 && two)) && is_a) {
+          qbuf[jw] = qs;
+          qv[jw] = qs * vsm[jw];
+        } else if ((lane == 0 || lane == 16) && !is_a) {
+          ubuf[jw < j ? jw : kPnb + jw - j] = qs;
         }
         u = __shfl_sync(0xffffffffu, un, 0);
       }
-    }
-    for (int x = r + G * warp; x < 2 * j; x += G * NW) {  // u = [W V]^T v over rows k+1..
-      const double* col = x < j ? Wp + L * x : Hv + L * (k0 + x - j);
-      double acc = 0.0;
-      for (int i = k + 1 + lane; i < n; i += 32) acc = fma(__ldcg(&col[i]), vsm[i], acc);
-      acc = warp_sum_xor(acc);
-      if (lane == 0) ubuf[x < j ? x : kPnb + x - j] = acc;
     }
     if (!barrier(mbase + 2u * j + 2u)) return;
     tprev = t;
