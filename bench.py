@@ -231,39 +231,55 @@ PREC = {"fp64": 0, "tf32": 1, "bf16": 2}
 DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
 
 # DRAM bytes per step of the dominant stage from one ncu capture, valid only
-# for the engine sources it was measured on (a SHA-256 of the CUDA sources
-# without comments): after any change to them the roofline's traffic is null
-# until it is measured again.
+# for the sources of that stage's kernels as they were measured (a SHA-256 of
+# the code without comments, stage_sources_sha): after any change to them the
+# roofline's traffic is null until it is measured again.
 #   reduction: dram__bytes_read.sum + dram__bytes_write.sum of k_trd_panel,
 #   k_trd_s2k_pack and k_trd_s2k over four generations of the first 32
-#   searches of the 256-search batch (22.96 GB, 5.74 GB per generation),
-#   scaled to the full batch by the sum of n^3 over the decompositions a step
-#   does (367.2e9 / 17.35e9 = 21.2). The full batch keeps more matrices in
-#   flight than L2 holds, so this is a lower bound on its traffic.
+#   searches of the 256-search batch, scaled to the full batch by the sum of
+#   n^3 over the decompositions a step does (367.2e9 / 17.35e9 = 21.2). The
+#   full batch keeps more matrices in flight than L2 holds, so this is a lower
+#   bound on its traffic.
 KERNEL_TRAFFIC = {
-    "reduction": {"bytes_per_step": 5.739e9 * 21.16, "sources_sha256_16": "0f83423a4fb2d80b",
-                  "capture": "batch256-first32, 4 generations, scaled by sum n^3"},
+    "reduction": {"bytes_per_step": 6.0366e9 * 21.16, "sources_sha256_16": "3e9600ff84ca6402",
+                  "capture": "batch256-first32, 4 generations (24.15 GB), scaled by sum n^3"},
+}
+
+# The code each stage's kernels are built from: the part of the tridiagonal
+# route's source up to the end of the reduction (its kernels and every helper
+# they call) and the headers they include.
+STAGE_SOURCES = {
+    "reduction": {"prefix": ("kernels_eig_trd.cu", "// Scans of one CTA over n entries"),
+                  "headers": ("device_common.cuh", "ozaki.cuh", "trd_common.cuh", "engine.h")},
 }
 
 
-def engine_sources_sha():
-    """Hash of the engine's CUDA/C++ sources with comments and blank lines
-    removed: a change to the code voids the recorded traffic, a change to a
-    comment does not."""
-    import glob
-    import hashlib
+def _strip_comments(text):
+    """The code without comments and blank lines (string and character
+    literals kept whole, so that "//" inside them is not a comment)."""
     import re
-    csrc = os.path.join(ROOT, "paper_2409_11765_gb300", "csrc")
-    files = sorted(glob.glob(os.path.join(csrc, "*.cu"))) + sorted(glob.glob(os.path.join(csrc, "*.cuh"))) \
-        + sorted(glob.glob(os.path.join(csrc, "*.h")))
-    # string and character literals are kept whole so that "//" inside them is not a comment
     token = re.compile(r'"(?:\\.|[^"\\\n])*"|\'(?:\\.|[^\'\\\n])*\'|//[^\n]*|/\*.*?\*/', re.S)
+    code = token.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", text)
+    lines = [ln.rstrip() for ln in code.splitlines()]
+    return "\n".join(ln for ln in lines if ln.strip())
+
+
+def stage_sources_sha(stage):
+    """Hash of the code a stage's kernels are built from (STAGE_SOURCES):
+    a change to it voids the recorded traffic, a change to a comment or to
+    another stage's kernels does not."""
+    import hashlib
+    spec = STAGE_SOURCES.get(stage)
+    if spec is None:
+        return None
+    csrc = os.path.join(ROOT, "paper_2409_11765_gb300", "csrc")
     h = hashlib.sha256()
-    for f in files:
-        text = open(f, encoding="utf-8").read()
-        code = token.sub(lambda m: m.group(0) if m.group(0)[0] in "\"'" else " ", text)
-        lines = [ln.rstrip() for ln in code.splitlines()]
-        h.update("\n".join(ln for ln in lines if ln.strip()).encode())
+    fname, marker = spec["prefix"]
+    text = open(os.path.join(csrc, fname), encoding="utf-8").read()
+    cut = text.find(marker)
+    h.update(_strip_comments(text[:cut] if cut >= 0 else text).encode())
+    for f in spec["headers"]:
+        h.update(_strip_comments(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 
@@ -483,7 +499,7 @@ def run_engine(args):
                                 if head == "tf32" else "MEASURED_PEAKS.json bf16")
     traffic = None
     kt = KERNEL_TRAFFIC.get(dom)
-    if kt and engine_sources_sha() == kt["sources_sha256_16"]:
+    if kt and stage_sources_sha(dom) == kt["sources_sha256_16"]:
         traffic = kt["bytes_per_step"]
     roofline = {"bound": bound, "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
                 "frac": achieved / peak if peak else None, "traffic": traffic, "kernel": dom,

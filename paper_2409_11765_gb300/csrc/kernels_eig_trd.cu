@@ -863,10 +863,12 @@ __device__ __forceinline__ int sturm_df(const float* dh, const float* dl, const 
 // LANES points per step, in three precisions: FP32 on the scaled block down to
 // a width of 2^-19 ||T||, widened by 2^-18 ||T|| (eight times the backward
 // error of an FP32 Sturm count, ~10 eps32 ||T||); double-float down to
-// 2^-41 ||T||, widened by 2^-40 ||T|| (over ten times that of a double-float
+// 2^-43 ||T||, widened by 2^-42 ||T|| (six times that of a double-float
 // count, ~10 2^-48 ||T||); each widened bracket checked with two counts of
 // the next precision (the previous bracket kept if the check fails), the
-// last step in FP64 to 4 eps64 ||T||.
+// last step in FP64 to 4 eps64 ||T||. The FP64 counts are the bulk of the
+// work (the FP64 pipe is ~80 % busy), so every precision goes as far as its
+// counts stay reliable.
 template <int LANES>
 __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
   int tile;
@@ -891,16 +893,12 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
     if (q == 0) lamb[t] = d[t];
     return;
   }
+  // the start bracket: [-||T||, ||T||] with ||T|| the largest Gershgorin row
+  // sum of the unsplit T (it holds every block's spectrum), widened for rounding
   const double tn = sc[0], pivmin = sc[1], scl = sc[7];
-  double gl = INFINITY, gu = -INFINITY;
-  for (int j = b0; j < b1; ++j) {
-    const double rad = (j > b0 ? fabs(es[j - 1]) : 0.0) + (j + 1 < b1 ? fabs(es[j]) : 0.0);
-    gl = fmin(gl, d[j] - rad);
-    gu = fmax(gu, d[j] + rad);
-  }
   const double atol = 4.0 * kTrdEps * tn;
   const double fudge = 2.0 * kTrdEps * tn * (b1 - b0) + 2.0 * pivmin;
-  double lo = gl - fudge, hi = gu + fudge;
+  double lo = -tn - fudge, hi = tn + fudge;
   const int idx = t - b0;
   // one multisection step on [lo, hi] from the counts of the LANES points
   auto narrow = [&](auto& lo_, auto& hi_, int cnt, auto w) -> bool {
@@ -943,11 +941,11 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_bisect(Search* S, TileMap tm) {
       }
     }
     // double-float
-    for (int it = 0; it < 60 && his - los > 0x1p-41; ++it) {
+    for (int it = 0; it < 60 && his - los > 0x1p-43; ++it) {
       const double w = (his - los) / (LANES + 1);
       if (!narrow(los, his, cnt_df(los + w * (q + 1)), w)) break;
     }
-    const double lo2 = fmax(lo, (los - 0x1p-40) / scl), hi2 = fmin(hi, (his + 0x1p-40) / scl);
+    const double lo2 = fmax(lo, (los - 0x1p-42) / scl), hi2 = fmin(hi, (his + 0x1p-42) / scl);
     if (lo2 < hi2 && check([&](double x) { return sturm64(d, e2, b0, b1, x, pivmin); }, lo2, hi2)) {
       lo = lo2;
       hi = hi2;
@@ -997,9 +995,9 @@ __global__ void __launch_bounds__(kTrdSortNT) k_trd_rank(Search* S, int s0) {
 
 // --------------------------------------------------------------------------
 // 4b. Inverse iteration (thread t, eigenvalue lamb[t] of its block): three
-// solves of (T - lambda I) x = x_prev by Gaussian elimination with partial
-// pivoting; the U factor's three diagonals go to scratch interleaved by
-// thread, the iterate lives in column t of ET.
+// solves of (T - lambda I) x = x_prev with one Gaussian elimination with
+// partial pivoting (its factors in scratch interleaved by thread), the
+// iterate in column t of ET.
 // --------------------------------------------------------------------------
 __device__ __forceinline__ double start_value(int t, int j) {
   uint32_t h = static_cast<uint32_t>(t) * 0x9E3779B1u ^ (static_cast<uint32_t>(j) * 0x85EBCA77u);
@@ -1010,6 +1008,8 @@ __device__ __forceinline__ double start_value(int t, int j) {
   h ^= h >> 15;
   return (static_cast<double>(h) + 0.5) * 0x1p-31 - 1.0;  // in (-1, 1)
 }
+
+constexpr long long kInvitSwap = 0x7ff8000000000000LL;  // a quiet NaN: the row-interchange flag
 
 __global__ void __launch_bounds__(kTrdTT) k_trd_invit(Search* S, TileMap tm) {
   int tile;
@@ -1034,44 +1034,63 @@ __global__ void __launch_bounds__(kTrdTT) k_trd_invit(Search* S, TileMap tm) {
   double* u1 = s.EG;
   double* u2 = s.EH;
   auto piv_of = [&](double a) { return fabs(a) > tiny ? a : (a < 0.0 ? -tiny : tiny); };
+  // factorisation of T - lambda I, once for the three solves: row j without
+  // an interchange keeps 1 / pivot (u0), its superdiagonal (u1) and the
+  // multiplier (u2); a row with one keeps the multiplier (u0) and the flag
+  // kInvitSwap in u1 (its U row, e_j, d_{j+1} - lambda, e_{j+1}, is read from
+  // T again when it is needed)
+  double a = d[b0] - lam, b = es[b0], c = 0.0;
+  for (int j = b0; j + 1 < b1; ++j) {
+    const double sub = es[j], nd = d[j + 1] - lam, nsup = (j + 2 < b1) ? es[j + 1] : 0.0;
+    const long long o = j * nn + t;
+    if (fabs(a) >= fabs(sub)) {
+      const double r = 1.0 / piv_of(a);
+      const double l = sub * r;
+      u0[o] = r;
+      u1[o] = b;
+      u2[o] = l;
+      a = nd - l * b;
+      b = nsup - l * c;
+    } else {
+      const double l = a / sub;
+      u0[o] = l;
+      u1[o] = __longlong_as_double(kInvitSwap);
+      const double a2 = b - l * nd;
+      b = c - l * nsup;
+      a = a2;
+    }
+    c = 0.0;
+  }
+  const double rlast = 1.0 / piv_of(a);
   for (int j = b0; j < b1; ++j) x[j] = start_value(t, j);
   for (int it = 0; it < 3; ++it) {
-    double a = d[b0] - lam, b = es[b0], c = 0.0;
+    // forward: the same row interchanges and multipliers on the iterate
     double y = x[b0];
     for (int j = b0; j + 1 < b1; ++j) {
-      const double sub = es[j], nd = d[j + 1] - lam, nsup = (j + 2 < b1) ? es[j + 1] : 0.0;
-      const double yn = x[j + 1];
       const long long o = j * nn + t;
-      if (fabs(a) >= fabs(sub)) {
-        const double piv = piv_of(a);
-        const double l = sub / piv;
-        u0[o] = piv;
-        u1[o] = b;
-        u2[o] = c;
+      const double yn = x[j + 1];
+      if (__double_as_longlong(u1[o]) != kInvitSwap) {
         x[j] = y;
-        y = yn - l * y;
-        a = nd - l * b;
-        b = nsup - l * c;
+        y = yn - u2[o] * y;
       } else {
-        const double l = a / sub;
-        u0[o] = sub;
-        u1[o] = nd;
-        u2[o] = nsup;
         x[j] = yn;
-        y = y - l * yn;
-        const double a2 = b - l * nd;
-        b = c - l * nsup;
-        a = a2;
+        y = y - u0[o] * yn;
       }
-      c = 0.0;
     }
     // back substitution, then normalise
-    double xn1 = y / piv_of(a), xn2 = 0.0;
+    double xn1 = y * rlast, xn2 = 0.0;
     x[b1 - 1] = xn1;
     double ss = xn1 * xn1;
     for (int j = b1 - 2; j >= b0; --j) {
       const long long o = j * nn + t;
-      const double v = (x[j] - u1[o] * xn1 - u2[o] * xn2) / u0[o];
+      const double ub = u1[o];
+      double v;
+      if (__double_as_longlong(ub) != kInvitSwap) {
+        v = (x[j] - ub * xn1) * u0[o];
+      } else {
+        const double nd = d[j + 1] - lam, nsup = (j + 2 < b1) ? es[j + 1] : 0.0;
+        v = (x[j] - nd * xn1 - nsup * xn2) / es[j];
+      }
       x[j] = v;
       xn2 = xn1;
       xn1 = v;
@@ -1374,8 +1393,17 @@ struct GemmSmem32 {
 // Step `pass` (0, 1, 2) maps ET -> EA, EA -> ET, ET -> EA: V' = V + V M, or a
 // copy when the previous step started from a defect small enough (then no M
 // was formed); the result is in EA after the three.
+// V' = V + V M on one 64 x 64 tile of V': 256 threads, each a 4 x 4 block of
+// consecutive rows and columns (float4 reads of the staged operands), k in
+// steps of 32 over the k tiles whose 64 x 64 block of M is flagged nonzero,
+// the next step's operands loaded into registers while the current one is
+// multiplied (two shared-memory buffers, one barrier per step). The products
+// are summed in ascending k, one FP32 FMA each.
+constexpr int kNsBK = 32;
+
 __global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass) {
-  __shared__ GemmSmem32 sm;
+  __shared__ __align__(16) float As[2][kNsBK][kGBM];      // V block, [k][i]
+  __shared__ __align__(16) float Bs[2][kNsBK][kGBN + 4];  // M block, [k][j] (rows 16-byte aligned)
   int tile;
   const int si = find_search(tm, tile);
   const Search& s = S[si];
@@ -1395,39 +1423,64 @@ __global__ void __launch_bounds__(kGNT) k_trd_ns(Search* S, TileMap tm, int pass
   }
   const float* M = reinterpret_cast<const float*>(s.EG);
   const int* flags = ti(s, TI_TFLAG);
-  float acc[4][4] = {};
-  for (int k0 = 0; k0 < n; k0 += kGBK) {
-    if (!__ldcg(&flags[k0 / kGBM + T * (j0 / kGBN)])) continue;  // M is zero on this tile
+  const int nkt = ceil_div(n, kNsBK);
+  auto next_kt = [&](int kt) {  // the first k step at or after kt on a flagged block of M
+    while (kt < nkt && !__ldcg(&flags[(kt * kNsBK) / kGBM + T * (j0 / kGBN)])) ++kt;
+    return kt;
+  };
+  float ra[8], rb[8];
+  auto load = [&](int kt) {
+    const int k0 = kt * kNsBK;
 #pragma unroll
-    for (int q = 0; q < 4; ++q) {
+    for (int q = 0; q < 8; ++q) {
       const int e = tid + q * kGNT;
-      const int ii = e & (kGBM - 1), kk = e >> 6;
+      const int ii = e & (kGBM - 1), kk = e >> 6;  // V: consecutive threads, consecutive rows
       const int gi = i0 + ii, gk = k0 + kk;
-      sm.As[kk][ii] = (gi < n && gk < n) ? static_cast<float>(V[gi + L * gk]) : 0.f;
-      const int kk2 = e & (kGBK - 1), jj = e >> 4;
+      ra[q] = (gi < n && gk < n) ? static_cast<float>(V[gi + L * gk]) : 0.f;
+      const int kk2 = e & (kNsBK - 1), jj = e >> 5;  // M: consecutive threads, consecutive k
       const int gk2 = k0 + kk2, gj = j0 + jj;
-      sm.Bs[kk2][jj] = (gk2 < n && gj < n) ? M[gk2 + L * gj] : 0.f;
+      rb[q] = (gk2 < n && gj < n) ? M[gk2 + L * gj] : 0.f;
     }
-    __syncthreads();
+  };
+  auto store = [&](int b) {
 #pragma unroll
-    for (int kk = 0; kk < kGBK; ++kk) {
-      float a[4], b[4];
-#pragma unroll
-      for (int r = 0; r < 4; ++r) a[r] = sm.As[kk][tr + 16 * r];
-#pragma unroll
-      for (int c = 0; c < 4; ++c) b[c] = sm.Bs[kk][tc + 16 * c];
+    for (int q = 0; q < 8; ++q) {
+      const int e = tid + q * kGNT;
+      As[b][e >> 6][e & (kGBM - 1)] = ra[q];
+      Bs[b][e & (kNsBK - 1)][e >> 5] = rb[q];
+    }
+  };
+  float acc[4][4] = {};
+  int kt = next_kt(0);
+  if (kt < nkt) {
+    load(kt);
+    store(0);
+  }
+  __syncthreads();
+  int b = 0;
+  while (kt < nkt) {
+    const int kn = next_kt(kt + 1);
+    if (kn < nkt) load(kn);
+#pragma unroll 8
+    for (int kk = 0; kk < kNsBK; ++kk) {
+      const float4 a4 = *reinterpret_cast<const float4*>(&As[b][kk][4 * tr]);
+      const float4 b4 = *reinterpret_cast<const float4*>(&Bs[b][kk][4 * tc]);
+      const float av[4] = {a4.x, a4.y, a4.z, a4.w}, bv[4] = {b4.x, b4.y, b4.z, b4.w};
 #pragma unroll
       for (int r = 0; r < 4; ++r)
 #pragma unroll
-        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(a[r], b[c], acc[r][c]);
+        for (int c = 0; c < 4; ++c) acc[r][c] = fmaf(av[r], bv[c], acc[r][c]);
     }
+    if (kn < nkt) store(b ^ 1);
     __syncthreads();
+    b ^= 1;
+    kt = kn;
   }
 #pragma unroll
-  for (int r = 0; r < 4; ++r)
+  for (int c = 0; c < 4; ++c)
 #pragma unroll
-    for (int c = 0; c < 4; ++c) {
-      const int i = i0 + tr + 16 * r, j = j0 + tc + 16 * c;
+    for (int r = 0; r < 4; ++r) {
+      const int i = i0 + 4 * tr + r, j = j0 + 4 * tc + c;
       if (i < n && j < n) Vo[i + L * j] = V[i + L * j] + static_cast<double>(acc[r][c]);
     }
 }
