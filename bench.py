@@ -241,8 +241,8 @@ DTYPE = {"fp64": "f64", "tf32": "tf32+f64", "bf16": "bf16+f64"}
 #   full batch keeps more matrices in flight than L2 holds, so this is a lower
 #   bound on its traffic.
 KERNEL_TRAFFIC = {
-    "reduction": {"bytes_per_step": 6.0366e9 * 21.16, "sources_sha256_16": "3e9600ff84ca6402",
-                  "capture": "batch256-first32, 4 generations (24.15 GB), scaled by sum n^3"},
+    "reduction": {"bytes_per_step": 6.0181e9 * 21.16, "sources_sha256_16": "601f2a358980cfb8",
+                  "capture": "batch256-first32, 4 generations (24.07 GB), scaled by sum n^3"},
 }
 
 # The code each stage's kernels are built from: the part of the tridiagonal

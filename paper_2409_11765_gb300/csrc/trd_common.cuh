@@ -62,10 +62,13 @@ __device__ __forceinline__ int* ti(const Search& s, int which) {
 constexpr int kBtNb = 128;  // reflectors per panel of the back-transformation
 constexpr int kPnb = kTrdPanel;  // columns per panel of the reduction
 constexpr int kPartStride = 2 * kPnb + 8;  // per-CTA partial sums of a reduction step
-// Back-transformation: blocked on the tensor cores above this size, one
-// register-resident column per warp in FP64 at and below it (where the
-// blocked form's fixed cost of six launches per panel dominates).
-constexpr int kBtBlockedMinN = 513;
+// Back-transformation: blocked on the tensor cores from this size on, one
+// register-resident column per warp in FP64 below it. The launches of the
+// blocked form are shared by every search of a batch, so in a large batch it
+// wins from n ~ 256 on (the 256-search batch: 146 -> 127 ms per generation
+// when its n = 500 searches moved to it); a lone n = 300 search is ~0.2 ms
+// slower in it than in the register form.
+constexpr int kBtBlockedMinN = 257;
 __host__ __device__ inline bool trd_bt_blocked(int n) { return n >= kBtBlockedMinN; }
 
 __host__ __device__ inline size_t trd_align256(size_t b) { return (b + 255) / 256 * 256; }
