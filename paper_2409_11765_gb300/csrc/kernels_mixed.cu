@@ -187,17 +187,15 @@ __global__ void __launch_bounds__(256, 1) k_tc_sample(Search* S, TileMap tm) {
   if (!ok && threadIdx.x == 0) atomicOr(s.err, 1);
 }
 
+void tc_set_attributes_once();
+
 void launch_tc_sample(Search* S, TileMap tm, int precision, cudaStream_t st) {
   if (tm.total <= 0) return;
-  if (precision == 2) {
-    const int bytes = TcPlan<1, false>::bytes;
-    cudaFuncSetAttribute(k_tc_sample<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_sample<1><<<tm.total, 256, bytes, st>>>(S, tm);
-  } else {
-    const int bytes = TcPlan<0, false>::bytes;
-    cudaFuncSetAttribute(k_tc_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_sample<0><<<tm.total, 256, bytes, st>>>(S, tm);
-  }
+  tc_set_attributes_once();
+  if (precision == 2)
+    k_tc_sample<1><<<tm.total, 256, TcPlan<1, false>::bytes, st>>>(S, tm);
+  else
+    k_tc_sample<0><<<tm.total, 256, TcPlan<0, false>::bytes, st>>>(S, tm);
 }
 
 // -------------------------------- objective ---------------------------------
@@ -296,15 +294,11 @@ __global__ void __launch_bounds__(256, 1) k_tc_objective(Search* S, TileMap tm) 
 
 void launch_tc_objective(Search* S, TileMap tm, int precision, cudaStream_t st) {
   if (tm.total <= 0) return;
-  if (precision == 2) {
-    const int bytes = TcPlan<1, true>::bytes;
-    cudaFuncSetAttribute(k_tc_objective<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_objective<1><<<tm.total, 256, bytes, st>>>(S, tm);
-  } else {
-    const int bytes = TcPlan<0, true>::bytes;
-    cudaFuncSetAttribute(k_tc_objective<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_objective<0><<<tm.total, 256, bytes, st>>>(S, tm);
-  }
+  tc_set_attributes_once();
+  if (precision == 2)
+    k_tc_objective<1><<<tm.total, 256, TcPlan<1, true>::bytes, st>>>(S, tm);
+  else
+    k_tc_objective<0><<<tm.total, 256, TcPlan<0, true>::bytes, st>>>(S, tm);
 }
 
 // ---------------------------- rank-mu update --------------------------------
@@ -375,15 +369,26 @@ __global__ void __launch_bounds__(256, 1) k_tc_cov_partial(Search* S, TileMap tm
 
 void launch_tc_cov_partial(Search* S, TileMap tm, int precision, cudaStream_t st) {
   if (tm.total <= 0) return;
-  if (precision == 2) {
-    const int bytes = TcPlan<1, true>::bytes;
-    cudaFuncSetAttribute(k_tc_cov_partial<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_cov_partial<1><<<tm.total, 256, bytes, st>>>(S, tm);
-  } else {
-    const int bytes = TcPlan<0, true>::bytes;
-    cudaFuncSetAttribute(k_tc_cov_partial<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
-    k_tc_cov_partial<0><<<tm.total, 256, bytes, st>>>(S, tm);
-  }
+  tc_set_attributes_once();
+  if (precision == 2)
+    k_tc_cov_partial<1><<<tm.total, 256, TcPlan<1, true>::bytes, st>>>(S, tm);
+  else
+    k_tc_cov_partial<0><<<tm.total, 256, TcPlan<0, true>::bytes, st>>>(S, tm);
+}
+
+// The dynamic shared memory of the six tensor-core GEMM kernels, set at the
+// first launch of any of them (the per-generation graphs replay the launches
+// without coming back here).
+void tc_set_attributes_once() {
+  static bool done = false;
+  if (done) return;
+  cudaFuncSetAttribute(k_tc_sample<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<0, false>::bytes);
+  cudaFuncSetAttribute(k_tc_sample<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<1, false>::bytes);
+  cudaFuncSetAttribute(k_tc_objective<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<0, true>::bytes);
+  cudaFuncSetAttribute(k_tc_objective<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<1, true>::bytes);
+  cudaFuncSetAttribute(k_tc_cov_partial<0>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<0, true>::bytes);
+  cudaFuncSetAttribute(k_tc_cov_partial<1>, cudaFuncAttributeMaxDynamicSharedMemorySize, TcPlan<1, true>::bytes);
+  done = true;
 }
 
 // C <- a C + c1 p_c p_c^T + c_mu (sum of the chunk partials, in chunk order),
