@@ -24,6 +24,7 @@ in FP64 by the oracle's objective, so a mixed-precision hit is a true hit.
 
     python tests/config_targets.py [--only LABEL-SUBSTRING] [--precision fp64|tf32]
                                    [--json out.json]
+    python tests/config_targets.py --markdown out.json     (the table of a saved run)
 """
 import argparse
 import json
@@ -127,13 +128,35 @@ def fp64_recheck(wl, best):
     return out
 
 
+def markdown(rows):
+    """The results table as it appears in the results notes."""
+    out = ["| configuration | path | target | reached | generations | candidates | time (s) | "
+           "candidates/s | best f (FP64 re-evaluated) | descents |",
+           "|---|---|---:|---|---:|---:|---:|---:|---:|---|"]
+    for r in rows:
+        reached = "yes" if r["reached"] else "no (budget)"
+        if r["searches"] > 10:
+            reached = "%d of %d searches" % (r["searches_at_target"], r["searches"])
+        d = r["descents"]
+        ds = str(d[0]) if len(d) == 1 else ("levels " + ",".join(map(str, d)))
+        out.append("| %s | %s | %.0e | %s | %d | %d | %.2f | %.3g | %.3e | %s |" % (
+            r["config"], r["precision"].upper(), r["f_target"], reached, r["generations"],
+            r["candidates"], r["seconds"], r["cand_per_s"], r["best_f_fp64"], ds))
+    return "\n".join(out)
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--only", default="")
     ap.add_argument("--precision", choices=["fp64", "tf32"], default=None)
     ap.add_argument("--json", default="")
     ap.add_argument("--seed", type=int, default=20240918)
+    ap.add_argument("--markdown", default="", help="print the table of a saved --json file and exit")
     args = ap.parse_args()
+    if args.markdown:
+        with open(args.markdown) as fh:
+            print(markdown(json.load(fh)))
+        return
     import __graft_entry__
     __graft_entry__.build()
     import paper_2409_11765_gb300 as eng

@@ -82,3 +82,11 @@ def test_generation_budget_without_a_hit():
     eng = _Script([(10, [1000], True)])
     c = CT.counting_run(eng, wl, 0, 1, 25, 60.0)
     assert c["hit_gen"] is None and c["gens"] == 25 and c["cand"] == 250
+
+
+def test_markdown_table():
+    row = dict(config="c", precision="tf32", f_target=1e-8, reached=True, generations=12,
+               candidates=310, seconds=0.5, cand_per_s=620.0, best_f_fp64=9e-9, searches=1,
+               searches_at_target=1, descents=[3])
+    lines = CT.markdown([row]).splitlines()
+    assert len(lines) == 3 and lines[2].startswith("| c | TF32 | 1e-08 | yes | 12 | 310 |")
